@@ -1,0 +1,219 @@
+"""Pins of the oracle's solvers and post-processing (no GPU).
+
+ACM (MNS section): the analytic plane Poiseuille flow is a fixed point of the
+discrete scheme to rounding (quadratic profile, m = 2 exact), a zero start
+converges to it, and its wall shear balances the body force exactly.
+LBM (MLBM section): velocity-set moments, equilibrium moments, collision
+invariants and relaxation rates of the TRT kernel, the lattice-shift limit of
+the meshless streaming step, uniform forcing on a periodic lattice.
+Geometry: closed-form porosity against Monte Carlo and against the porosity
+range printed in the case definition section; probe flux conservation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+# ---------------------------------------------------------------- geometry
+def test_porosity_printed_range():
+    # the case definition section: r in [0.04, 0.69] gives phi in [0.05, 0.9997]
+    assert round(oracle.porosity(0.04), 4) == 0.9997
+    assert round(oracle.porosity(0.69), 2) == 0.05
+
+
+@pytest.mark.parametrize("r", [0.2, 0.45, 0.55, 0.62, 0.69])
+def test_porosity_and_area_monte_carlo(r):
+    rng = np.random.default_rng(7)
+    x = rng.random((2_000_000, 3))
+    s = oracle.sdf(x, (0.5, 0.5, 0.5), r)
+    phi_mc = (s >= 0).mean()
+    assert abs(phi_mc - oracle.porosity(r)) < 2e-3
+    eps = 0.01
+    area_mc = (np.abs(s) < eps).mean() / (2 * eps)
+    assert abs(area_mc - oracle.wall_area(r)) < 0.02 * oracle.wall_area(r) + 0.01
+
+
+# ---------------------------------------------------------------- ACM
+@pytest.fixture(scope="module")
+def chan():
+    ch = synth.channel(h=0.05, H=0.5)
+    idx = oracle.knn(ch["xyz"], ch["xyz"], 25)
+    w4 = oracle.acm_weights(ch["xyz"], idx)
+    wl, idxb = oracle.neumann_stencils(ch, 25)
+    wgb = oracle.neumann_weights(ch, idxb)
+    dmin = np.linalg.norm(oracle.min_image(ch["xyz"][idx[:, 1]] - ch["xyz"]), axis=1).min()
+    dt = oracle.acm_dt(dmin, 1.0)
+    y = ch["xyz"][:, 1]
+    exact = np.zeros((ch.n, 4))
+    exact[:, 0] = y * (0.5 - y) / 2.0  # v_x = g y (H - y) / (2 nu), g = nu = 1
+    exact[ch["type"] == 1, 0] = 0.0
+    return dict(case=ch, idx=idx, w4=w4, wl=wl, idxb=idxb, wgb=wgb, dt=dt, exact=exact)
+
+
+def test_poiseuille_is_fixed_point(chan):
+    c = chan
+    out, res = oracle.acm_run(c["case"], c["idx"], c["w4"], c["idxb"], c["wgb"], c["exact"], 40,
+                              dt=c["dt"], v_ref=0.01)
+    assert np.abs(out - c["exact"]).max() <= 1e-12 * c["exact"][:, 0].max()
+    # a wrong sign on the body force or viscosity would move it at once
+    bad, _ = oracle.acm_run(c["case"], c["idx"], c["w4"], c["idxb"], c["wgb"], c["exact"], 40,
+                            g=(-1.0, 0.0, 0.0), dt=c["dt"], v_ref=0.01)
+    assert np.abs(bad - c["exact"]).max() > 1e-4
+
+
+def test_poiseuille_from_rest(chan):
+    c = chan
+    out, res = oracle.acm_run(c["case"], c["idx"], c["w4"], c["idxb"], c["wgb"], np.zeros_like(c["exact"]),
+                              6000, dt=c["dt"], v_ref=0.01)
+    err = np.abs(out[:, :3] - c["exact"][:, :3]).max() / c["exact"][:, 0].max()
+    assert err < 1e-4, err
+    assert res[-1] < res[100]
+
+
+def test_poiseuille_wall_force_balance(chan):
+    # F_x on the two walls equals the body force on the fluid slab g H (per unit
+    # cell area 1): Eqs. stress_tensor_force and integration_force with A = 2.
+    c = chan
+    ex = c["exact"].copy()
+    F = oracle.drag(c["case"], c["idx"], c["w4"][c["wl"]][:, :3], ex, nu=1.0, area=2.0)
+    assert abs(F[0] - 0.5) < 1e-10 and abs(F[1]) < 1e-10 and abs(F[2]) < 1e-10
+
+
+def test_permeability_of_poiseuille(chan):
+    # channel probes: the mean over the five planes of the midpoint-rule flux of
+    # v_x = y (H - y)/2 on 0 < y < H=0.5 (zero in the solid slab) = H^3 / 12
+    c = chan
+    ch = c["case"]
+    allpts = oracle.probe_points(64)
+    fluid = allpts[:, 1] < 0.5  # the slab 0.5 < y < 1 is solid
+    pts = allpts[fluid]
+    idx = oracle.knn(ch["xyz"], pts, 25)
+    w = oracle.rbf_weights(ch["xyz"], pts, idx, 3, 2, [(oracle.OP_INTERP, (0, 0, 0))], centre_is_node=False)
+    probes = dict(points=allpts, fluid=fluid, idx=idx, w=w)
+    k, q = oracle.permeability(probes, c["exact"][:, 0], 1.0, 1.0)
+    ys = (np.arange(64) + 0.5) / 64
+    mid = (ys[ys < 0.5] * (0.5 - ys[ys < 0.5]) / 2).sum() / 64  # exact midpoint sum
+    assert abs(q - mid) < 1e-10
+    assert abs(q - 0.5 ** 3 / 12) < 1e-4
+
+
+# ---------------------------------------------------------------- LBM
+@pytest.mark.parametrize("q", [15, 19])
+def test_velocity_set_moments(q):
+    e, w, opp = oracle.velocity_set(q)
+    cs2 = 1.0 / 3.0
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose((w[:, None] * e).sum(0), 0.0)
+    assert np.allclose(np.einsum("k,ka,kb->ab", w, e, e), cs2 * np.eye(3))
+    I = np.eye(3)
+    iso = cs2 ** 2 * (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+                      + np.einsum("ad,bc->abcd", I, I))
+    assert np.allclose(np.einsum("k,ka,kb,kc,kd->abcd", w, e, e, e, e), iso)
+    assert np.array_equal(e[opp], -e)
+    if q == 15:  # the paper's table of weights
+        assert np.allclose(w[[0, 1, 7]], [2 / 9, 1 / 9, 1 / 72])
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_equilibrium_moments(q):
+    rng = np.random.default_rng(1)
+    rho = 1 + 0.01 * rng.standard_normal(50)
+    v = 0.01 * rng.standard_normal((50, 3))
+    feq = oracle.lbm_equilibrium(q, rho, v)
+    e, _, _ = oracle.velocity_set(q)
+    assert np.allclose(feq.sum(0), rho, rtol=0, atol=1e-15)
+    assert np.allclose((e.T @ feq).T, rho[:, None] * v, rtol=0, atol=1e-15)
+    pi = np.einsum("ka,kb,kn->nab", e, e, feq)
+    want = rho[:, None, None] * (np.eye(3)[None] / 3 + v[:, :, None] * v[:, None, :])
+    assert np.allclose(pi, want, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_collision_invariants_and_rates(q):
+    rng = np.random.default_rng(2)
+    n = 64
+    e, w, opp = oracle.velocity_set(q)
+    rho = 1 + 0.01 * rng.standard_normal(n)
+    v = 0.01 * rng.standard_normal((n, 3))
+    g = np.array([1e-5, -2e-5, 3e-6])
+    tp, tm = 0.8, oracle.tau_minus(0.8, 3.0 / 16.0)
+    assert abs(tm - 1.125) < 1e-15
+    feq = oracle.lbm_equilibrium(q, rho, v)
+    # equilibrium collides to itself plus the force term
+    post = oracle.lbm_collide(feq, q, tp, tm, g)
+    F = w[:, None] * 3.0 * (e @ g)[:, None] * rho[None, :]
+    assert np.allclose(post - feq, F, rtol=0, atol=1e-15)
+    # mass conserved exactly, momentum gains rho g
+    f = feq + 1e-3 * rng.standard_normal(feq.shape) * w[:, None]
+    post = oracle.lbm_collide(f, q, tp, tm, g)
+    assert np.allclose(post.sum(0), f.sum(0), rtol=0, atol=1e-15)
+    mom_in = (e.T @ f).T
+    rho_f = f.sum(0)
+    assert np.allclose((e.T @ post).T - mom_in, rho_f[:, None] * g, rtol=0, atol=1e-15)
+    # symmetric / antisymmetric non-equilibrium parts relax by 1 - 1/tau+- (no force)
+    z = np.zeros(3)
+    f0 = oracle.lbm_equilibrium(q, np.ones(n), np.zeros((n, 3)))
+    d = 1e-4 * rng.standard_normal(f0.shape)
+    d[0] = 0.0
+    sym = 0.5 * (d + d[opp])
+    sym -= w[:, None] * sym.sum(0)[None]  # no mass change; symmetric => no momentum
+    post_s = oracle.lbm_collide(f0 + sym, q, tp, tm, z)
+    assert np.allclose(post_s - f0, (1 - 1 / tp) * sym, rtol=0, atol=1e-13)
+    anti = 0.5 * (d - d[opp])  # antisymmetric => no mass change
+    anti -= w[:, None] * 3.0 * (e @ (e.T @ anti))  # remove its momentum
+    post_a = oracle.lbm_collide(f0 + anti, q, tp, tm, z)
+    assert np.allclose(post_a - f0, (1 - 1 / tm) * anti, rtol=0, atol=1e-13)
+
+
+def test_streaming_reduces_to_lattice_shift():
+    # Nodes on an exact cubic lattice with spacing a and dx = a: every departure
+    # point x_i - a e_k is a node in the 27-point stencil, where the RBF-FD
+    # interpolant equals the node value, so streaming is the lattice shift.
+    n_axis = 8
+    lat = synth.lattice(n_axis)
+    a = 1.0 / n_axis
+    idx = oracle.knn(lat["xyz"], lat["xyz"], 27)
+    for q in (15, 19):
+        e, _, _ = oracle.velocity_set(q)
+        wk = oracle.lbm_weights(lat["xyz"], idx, q, a)
+        rng = np.random.default_rng(q)
+        fpost = rng.random((q, lat.n))
+        f = oracle.lbm_stream(fpost, q, lat, idx, wk)
+        grid = fpost.reshape(q, n_axis, n_axis, n_axis)
+        for k in range(q):
+            shifted = np.roll(grid[k], shift=tuple(e[k].astype(int)), axis=(0, 1, 2)).ravel()
+            assert np.allclose(f[k], shifted, rtol=0, atol=1e-12), k
+
+
+def test_uniform_forcing_on_periodic_lattice():
+    # no walls, uniform force: the mean velocity grows by exactly g_lb per step
+    lat = synth.lattice(6)
+    idx = oracle.knn(lat["xyz"], lat["xyz"], 27)
+    q = 19
+    wk = oracle.lbm_weights(lat["xyz"], idx, q, 1.0 / 6)
+    f0 = oracle.lbm_equilibrium(q, np.ones(lat.n), np.zeros((lat.n, 3)))
+    g = np.array([2e-6, 0.0, -1e-6])
+    f = oracle.lbm_run(f0, q, lat, idx, wk, 0.8, 1.125, g, 25)
+    mac = oracle.lbm_macro(f, q)
+    assert np.allclose(mac[:, :3], 25 * g[None, :], rtol=1e-9, atol=1e-15)
+    assert np.allclose(mac[:, 3], 1.0, rtol=0, atol=1e-14)
+
+
+def test_lbm_units():
+    u = oracle.lbm_units(nu=1.0, tau_plus=0.8, dx=0.004, g=(1.0, 0, 0))
+    assert abs(u["nu_lb"] - 0.1) < 1e-15
+    assert abs(u["dt"] - 1.6e-6) < 1e-18
+    assert abs(u["g_lb"][0] - 6.4e-10) < 1e-22
+    # the paper's footnote: dt from 1.04e-6 to 1.67e-5 for dx = h_min / 2,
+    # h_min in [0.005, 0.02] at tau+ = 1 (nu_lb = 1/6), nu = 1
+    lo = oracle.lbm_units(1.0, 1.0, 0.0025, (1, 0, 0))["dt"]
+    hi = oracle.lbm_units(1.0, 1.0, 0.01, (1, 0, 0))["dt"]
+    assert abs(lo - 1.04e-6) < 0.01e-6 and abs(hi - 1.67e-5) < 0.01e-5
+
+
+def test_acm_dt_footnote():
+    # the MNS section's footnote: dt from 1.25e-6 to 2e-5 for h_min in [0.005, 0.02]
+    assert abs(oracle.acm_dt(0.005, 1.0) - 1.25e-6) < 1e-20
+    assert abs(oracle.acm_dt(0.02, 1.0) - 2e-5) < 1e-20
