@@ -1,0 +1,193 @@
+/* rbfgb.h — C ABI of the GB300 (sm_103a) meshless porous-media solvers.
+ *
+ * The library implements the hot path of Strzelczyk, Rot, Kosec & Matyka,
+ * "Cross-validation of meshless Navier-Stokes solvers in porous media flows"
+ * (arXiv 2404.14195): RBF-FD stencil weights (PHS + monomials), the explicit
+ * artificial-compressibility Navier-Stokes step (MNS) and the two-relaxation-time
+ * meshless lattice Boltzmann step (MLBM) on scattered nodes, and the permeability
+ * and drag reductions.  The calls follow the paper's statement of the problem:
+ * nodes and geometry in; stencils and weights; step to steady state; drag
+ * coefficient and permeability out.
+ *
+ * Conventions (every call):
+ *  - returns RBF_OK (0) or a negative RBF_E* code; rbf_last_error() gives the
+ *    message of the last failure on that context (owned by the context);
+ *  - host arrays passed in are owned by the caller and copied before return;
+ *    host arrays passed out are written before return (the call synchronises
+ *    the context's stream);
+ *  - node arrays are in the caller's node order (the library reorders nodes
+ *    along a Morton curve internally and maps back on output);
+ *  - a context is bound to one device and one CUDA stream; calls on one context
+ *    are not thread-safe; all device work is ordered on that stream;
+ *  - there is no CPU fallback: without a usable CUDA device rbf_create fails
+ *    with RBF_ECUDA.
+ */
+#ifndef RBFGB_H
+#define RBFGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RBF_OK = 0,
+    RBF_EINVAL = -1,        /* bad argument, size or call order */
+    RBF_ECUDA = -2,         /* CUDA runtime or launch error */
+    RBF_ESINGULAR = -3,     /* a stencil's saddle-point system had a zero pivot */
+    RBF_EDIVERGED = -4,     /* non-finite field values appeared */
+    RBF_ENOTCONVERGED = -5, /* step cap reached before the stopping criterion */
+    RBF_ETIMEOUT = -6,      /* a device-side wait hit its iteration cap */
+    RBF_ENOMEM = -7         /* device allocation failed */
+};
+
+enum { RBF_SOLVER_ACM = 0, RBF_SOLVER_LBM = 1 };
+enum { RBF_FP64 = 0, RBF_FP32 = 1 };
+enum { RBF_FLUID = 0, RBF_WALL = 1 };
+/* operator ids for rbf_get_weights */
+enum {
+    RBF_OP_DX = 0, RBF_OP_DY = 1, RBF_OP_DZ = 2, RBF_OP_LAP = 3, /* ACM node operators */
+    RBF_OP_LBM0 = 16                                            /* LBM: RBF_OP_LBM0 + k, k = 1..q-1 */
+};
+
+typedef struct rbf_ctx rbf_ctx;
+
+/* Create a context on `device`.  cuda_stream: a cudaStream_t to order all work
+ * on, or NULL for a stream the context creates and owns. */
+int rbf_create(rbf_ctx **out, int device, void *cuda_stream);
+int rbf_destroy(rbf_ctx *ctx);
+const char *rbf_last_error(const rbf_ctx *ctx);
+
+/* Nodes of the discretisation (meshless discretisation section).  n >= 2.
+ *  xyz    n x 3 doubles in the periodic unit cell [0,1)^3 (cell side d = 1);
+ *  type   n bytes, RBF_FLUID or RBF_WALL (wall nodes lie on the grain surface);
+ *  normal n x 3 doubles; on wall nodes the unit normal pointing out of the solid
+ *         into the fluid, ignored on fluid nodes (may be NULL if no wall nodes).
+ * Resets stencils, weights and fields. */
+int rbf_set_nodes(rbf_ctx *ctx, int64_t n, const double *xyz, const uint8_t *type,
+                  const double *normal);
+
+/* The grain: a sphere of radius r centred at c in the periodic cell (case
+ * definition section).  Used for the solid mask of the permeability probes, the
+ * wall area A of the drag quadrature and the porosity in the drag coefficient. */
+int rbf_set_sphere(rbf_ctx *ctx, const double c[3], double r);
+
+/* Stencils S_i: the n_l nearest nodes of every node by periodic distance, ordered
+ * by (squared distance, caller's node index), so S_i(1) = i (meshless
+ * discretisation section).  Wall nodes also get a Neumann stencil: the node
+ * itself and its n_l - 1 nearest fluid nodes.  2 <= n_l <= 64. */
+int rbf_build_stencils(rbf_ctx *ctx, int n_l);
+
+/* Copy the stencils out: idx (n x n_l) caller's node indices. */
+int rbf_get_stencils(rbf_ctx *ctx, int32_t *idx);
+
+typedef struct {
+    int64_t n_systems;   /* saddle systems solved */
+    int64_t n_singular;  /* systems with a zero pivot (their weights are NaN) */
+    double h_min;        /* smallest internodal distance min_i delta_i */
+} rbf_weight_report;
+
+/* RBF-FD weights, Eqs. operatorApprox, rbfScaling and augmentedSystem: PHS
+ * r^phs_k (odd, >= 3) in the distance scaled by delta_i (distance from x_i to its
+ * nearest neighbour), augmented with the C(mono_m + 3, 3) monomials of degree
+ * <= mono_m; solved per node in FP64 by LU with partial pivoting.
+ *  solver RBF_SOLVER_ACM: d/dx, d/dy, d/dz, Laplacian at every node, plus the
+ *         gradient on every wall node's Neumann stencil.
+ *  solver RBF_SOLVER_LBM: interpolation to the departure points x_i - dx e_k
+ *         (k = 1..q-1, q = 15 or 19) at every node (MLBM section, L = 1), plus
+ *         the gradient at wall nodes for the stress tensor.
+ * Requires n_l >= C(mono_m + 3, 3).  rep may be NULL.  Returns RBF_ESINGULAR when
+ * any system was singular (weights of those nodes are NaN). */
+int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, double dx,
+                        rbf_weight_report *rep);
+
+/* Copy one operator's FP64 weights out: out (n x n_l), caller's node order, row i
+ * the weights of node i over its stencil rbf_get_stencils()[i]. */
+int rbf_get_weights(rbf_ctx *ctx, int op, double *out);
+
+typedef struct {
+    int precision;   /* RBF_FP64 or RBF_FP32: storage and arithmetic of the steps */
+    double nu;       /* kinematic viscosity */
+    double g[3];     /* body acceleration */
+    double rho;      /* density (ACM) / reference density (LBM); 0 -> 1 */
+    /* ACM (MNS section) */
+    double dt;       /* time step; <= 0 -> cfl * h_min^2 / (2 nu) */
+    double cfl;      /* 0 -> 0.1 */
+    double beta;     /* compressibility parameter of Eq. MNS_C; 0 -> 10 */
+    double v_ref;    /* reference speed of Eq. MNS_C; <= 0 -> 0.01 |g| d^2 / nu */
+    int n_p;         /* pressure iterations per step; 0 -> 3 */
+    /* LBM (MLBM section) */
+    double tau_plus; /* 0 -> 0.8 */
+    double magic;    /* TRT Lambda = (tau+ - 1/2)(tau- - 1/2); 0 -> 3/16 */
+} rbf_params;
+
+/* Allocate and initialise the fields of the solver chosen in
+ * rbf_compute_weights: ACM v = p = 0; LBM f = f_eq(rho = 1, v = 0) (MLBM section's
+ * initial condition).  Resets the step counter. */
+int rbf_init(rbf_ctx *ctx, const rbf_params *p);
+
+/* Advance nsteps explicit steps (MNS or MLBM algorithm of the appendix). */
+int rbf_step(rbf_ctx *ctx, int nsteps);
+
+/* Fields in physical units, caller's node order: uvwp (n x 4) = (u, v, w, p).
+ * LBM: v = (dx/dt) v_lb of the last pre-collision state, p = rho_ref (dx/dt)^2
+ * (rho_lb - <rho_lb>) c_s^2. */
+int rbf_get_fields(rbf_ctx *ctx, double *uvwp);
+/* Set the ACM state (u, v, w, p) (a warm start or a restart); C of Eq. MNS_C is
+ * recomputed from the new velocity.  LBM contexts: RBF_EINVAL. */
+int rbf_set_fields(rbf_ctx *ctx, const double *uvwp);
+
+/* LBM populations, unshifted, FP64, q x n (population-major), caller's node
+ * order: the post-collision state the next step streams. */
+int rbf_lbm_get_populations(rbf_ctx *ctx, double *f);
+int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f);
+
+/* Permeability, Eq. k_definition: probes on an m_p x m_p midpoint grid on each of
+ * the planes x = 0, .2, .4, .6, .8; fluid probes interpolate v_x from their own
+ * n_l nearest nodes (L = 1 weights centred at the probe), solid probes count as
+ * zero; q = probe mean; k/d^2 = q nu / |g|.  FP64 accumulation.  Needs
+ * rbf_set_sphere.  The probe set is built on the first call and when m_p changes. */
+int rbf_permeability(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q);
+
+/* Hydrodynamic force on the grain, Eqs. stress_tensor_force and
+ * integration_force, F = (A / N_b) sum_b sigma . n over wall nodes, and the drag
+ * coefficient K = F_x / (6 pi r phi q mu) of Eq. K_definition with q from
+ * rbf_permeability(m_p).  FP64 accumulation. */
+int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K);
+
+/* Relative velocity change |v - v_prev|_2 / |v|_2 over fluid nodes over the last
+ * step (ACM), FP64 accumulation; computed when the last rbf_step ran with
+ * residual tracking (rbf_solve does).  */
+typedef struct {
+    int64_t max_steps;   /* step cap */
+    int check_every;     /* steps between convergence checks; 0 -> 100 */
+    double tol;          /* ACM: relative velocity change per step; LBM: relative
+                            change of k/d^2 between checks */
+    int m_p;             /* probes per plane side for LBM checks; 0 -> 32 */
+} rbf_solve_opts;
+
+typedef struct {
+    int64_t steps;       /* steps taken by this call */
+    double residual;     /* last criterion value */
+    double k_over_d2;    /* permeability at the end (probe grid m_p) */
+    int converged;
+} rbf_solve_result;
+
+/* Step until the criterion holds or max_steps: returns RBF_OK or
+ * RBF_ENOTCONVERGED (res filled in both cases), RBF_EDIVERGED on non-finite
+ * fields. */
+int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res);
+
+/* Device time of the last rbf_step (milliseconds, CUDA events on the context
+ * stream), and the mean duration of one launch of the dominant step kernel over
+ * that call (the fused LBM kernel; the ACM predictor).  */
+int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int64_t *kernel_launches);
+
+/* Number of kernel launches issued by this context since creation. */
+int64_t rbf_launch_count(const rbf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

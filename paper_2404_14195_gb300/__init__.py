@@ -1,0 +1,255 @@
+"""Python binding of librbfgb — the GB300 (sm_103a) meshless porous-media solvers
+of arXiv 2404.14195 (RBF-FD stencils and weights, the artificial-compressibility
+Navier-Stokes step, the TRT meshless lattice Boltzmann step, permeability and
+drag).
+
+Argument marshalling only: every call goes through the C ABI declared in
+``include/rbfgb.h`` and every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback: importing works anywhere, but creating a
+``Solver`` raises ``RbfError`` when the CUDA library is missing or no GPU is
+usable.
+
+The ``rbf_*`` names of the C ABI are exported as ctypes functions by ``lib()``;
+``Solver`` wraps one ``rbf_ctx`` with numpy in and out.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+RBF_OK, RBF_EINVAL, RBF_ECUDA, RBF_ESINGULAR = 0, -1, -2, -3
+RBF_EDIVERGED, RBF_ENOTCONVERGED, RBF_ETIMEOUT, RBF_ENOMEM = -4, -5, -6, -7
+RBF_SOLVER_ACM, RBF_SOLVER_LBM = 0, 1
+RBF_FP64, RBF_FP32 = 0, 1
+RBF_OP_DX, RBF_OP_DY, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_LBM0 = 0, 1, 2, 3, 16
+
+_ERRNAMES = {RBF_EINVAL: "EINVAL", RBF_ECUDA: "ECUDA", RBF_ESINGULAR: "ESINGULAR",
+             RBF_EDIVERGED: "EDIVERGED", RBF_ENOTCONVERGED: "ENOTCONVERGED",
+             RBF_ETIMEOUT: "ETIMEOUT", RBF_ENOMEM: "ENOMEM"}
+
+
+class RbfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rbf_weight_report(ctypes.Structure):
+    _fields_ = [("n_systems", ctypes.c_int64), ("n_singular", ctypes.c_int64), ("h_min", ctypes.c_double)]
+
+
+class rbf_params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("nu", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("rho", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("beta", ctypes.c_double), ("v_ref", ctypes.c_double), ("n_p", ctypes.c_int),
+                ("tau_plus", ctypes.c_double), ("magic", ctypes.c_double)]
+
+
+class rbf_solve_opts(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
+                ("m_p", ctypes.c_int)]
+
+
+class rbf_solve_result(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("residual", ctypes.c_double), ("k_over_d2", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# C ABI: name -> (restype, argtypes)
+_P, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+ABI = {
+    "rbf_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "rbf_destroy": (_I, [_P]),
+    "rbf_last_error": (ctypes.c_char_p, [_P]),
+    "rbf_set_nodes": (_I, [_P, _I64, _P, _P, _P]),
+    "rbf_set_sphere": (_I, [_P, _P, _D]),
+    "rbf_build_stencils": (_I, [_P, _I]),
+    "rbf_get_stencils": (_I, [_P, _P]),
+    "rbf_compute_weights": (_I, [_P, _I, _I, _I, _I, _D, ctypes.POINTER(rbf_weight_report)]),
+    "rbf_get_weights": (_I, [_P, _I, _P]),
+    "rbf_init": (_I, [_P, ctypes.POINTER(rbf_params)]),
+    "rbf_step": (_I, [_P, _I]),
+    "rbf_get_fields": (_I, [_P, _P]),
+    "rbf_set_fields": (_I, [_P, _P]),
+    "rbf_lbm_get_populations": (_I, [_P, _P]),
+    "rbf_lbm_set_populations": (_I, [_P, _P]),
+    "rbf_permeability": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "rbf_drag": (_I, [_P, _I, _P, ctypes.POINTER(_D)]),
+    "rbf_solve": (_I, [_P, ctypes.POINTER(rbf_solve_opts), ctypes.POINTER(rbf_solve_result)]),
+    "rbf_last_step_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "rbf_launch_count": (_I64, [_P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load librbfgb.so (built in-tree by ``_build.build()``); raises if missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RbfError(RBF_ECUDA, f"CUDA library not built: {path} (run __graft_entry__.build())")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in ABI.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One case on one GPU: nodes, stencils, weights, fields (an ``rbf_ctx``)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        rc = L.rbf_create(ctypes.byref(h), device, stream)
+        if rc != RBF_OK:
+            raise RbfError(rc, "rbf_create failed (no usable CUDA device?)")
+        self._h = h
+        self.n = 0
+        self.n_l = 0
+        self.q = 0
+        self.solver = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rbf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, rc):
+        if rc != RBF_OK:
+            raise RbfError(rc, self._L.rbf_last_error(self._h).decode())
+        return rc
+
+    # -- nodes and geometry -------------------------------------------------
+    def set_nodes(self, xyz, type_, normal=None):
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        t = np.ascontiguousarray(type_, np.uint8)
+        nrm = None if normal is None else np.ascontiguousarray(normal, np.float64)
+        self._ck(self._L.rbf_set_nodes(self._h, len(xyz), _ptr(xyz), _ptr(t), None if nrm is None else _ptr(nrm)))
+        self.n = len(xyz)
+
+    def set_sphere(self, c, r):
+        c = np.ascontiguousarray(c, np.float64)
+        self._ck(self._L.rbf_set_sphere(self._h, _ptr(c), float(r)))
+
+    def set_case(self, case):
+        self.set_nodes(case["xyz"], case["type"], case["normal"])
+        if case.get("centre") is not None and case.get("radius", 0) > 0:
+            self.set_sphere(case["centre"], case["radius"])
+
+    # -- stencils and weights ----------------------------------------------
+    def build_stencils(self, n_l: int):
+        self._ck(self._L.rbf_build_stencils(self._h, n_l))
+        self.n_l = n_l
+
+    def get_stencils(self):
+        out = np.empty((self.n, self.n_l), np.int32)
+        self._ck(self._L.rbf_get_stencils(self._h, _ptr(out)))
+        return out
+
+    def compute_weights(self, k: int = 3, m: int = 2, solver: int = RBF_SOLVER_ACM, q: int = 19, dx: float = 0.0):
+        rep = rbf_weight_report()
+        rc = self._L.rbf_compute_weights(self._h, k, m, solver, q, dx, ctypes.byref(rep))
+        self._ck(rc)
+        self.solver = solver
+        self.q = q if solver == RBF_SOLVER_LBM else 0
+        return dict(n_systems=rep.n_systems, n_singular=rep.n_singular, h_min=rep.h_min)
+
+    def get_weights(self, op: int):
+        out = np.empty((self.n, self.n_l), np.float64)
+        self._ck(self._L.rbf_get_weights(self._h, op, _ptr(out)))
+        return out
+
+    # -- time stepping --------------------------------------------------------
+    def init(self, precision=RBF_FP64, nu=1.0, g=(1.0, 0.0, 0.0), rho=1.0, dt=0.0, cfl=0.1, beta=10.0,
+             v_ref=0.0, n_p=3, tau_plus=0.8, magic=3.0 / 16.0):
+        p = rbf_params()
+        p.precision = precision
+        p.nu = nu
+        p.g[0], p.g[1], p.g[2] = g
+        p.rho, p.dt, p.cfl, p.beta, p.v_ref, p.n_p = rho, dt, cfl, beta, v_ref, n_p
+        p.tau_plus, p.magic = tau_plus, magic
+        self._ck(self._L.rbf_init(self._h, ctypes.byref(p)))
+
+    def step(self, nsteps: int):
+        self._ck(self._L.rbf_step(self._h, int(nsteps)))
+
+    def get_fields(self):
+        out = np.empty((self.n, 4), np.float64)
+        self._ck(self._L.rbf_get_fields(self._h, _ptr(out)))
+        return out
+
+    def set_fields(self, uvwp):
+        a = np.ascontiguousarray(uvwp, np.float64)
+        assert a.shape == (self.n, 4)
+        self._ck(self._L.rbf_set_fields(self._h, _ptr(a)))
+
+    def lbm_get_populations(self):
+        out = np.empty((self.q, self.n), np.float64)
+        self._ck(self._L.rbf_lbm_get_populations(self._h, _ptr(out)))
+        return out
+
+    def lbm_set_populations(self, f):
+        a = np.ascontiguousarray(f, np.float64)
+        assert a.shape == (self.q, self.n)
+        self._ck(self._L.rbf_lbm_set_populations(self._h, _ptr(a)))
+
+    # -- outputs --------------------------------------------------------------
+    def permeability(self, m_p: int = 32):
+        k, q = ctypes.c_double(), ctypes.c_double()
+        self._ck(self._L.rbf_permeability(self._h, m_p, ctypes.byref(k), ctypes.byref(q)))
+        return k.value, q.value
+
+    def drag(self, m_p: int = 32):
+        F = np.zeros(3)
+        K = ctypes.c_double()
+        self._ck(self._L.rbf_drag(self._h, m_p, _ptr(F), ctypes.byref(K)))
+        return F, K.value
+
+    def solve(self, max_steps: int, tol: float, check_every: int = 100, m_p: int = 32, raise_on_cap=False):
+        o = rbf_solve_opts(max_steps, check_every, tol, m_p)
+        r = rbf_solve_result()
+        rc = self._L.rbf_solve(self._h, ctypes.byref(o), ctypes.byref(r))
+        if rc not in (RBF_OK, RBF_ENOTCONVERGED) or (raise_on_cap and rc != RBF_OK):
+            self._ck(rc)
+        return dict(steps=r.steps, residual=r.residual, k_over_d2=r.k_over_d2, converged=bool(r.converged))
+
+    def last_step_timing(self):
+        t, k, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        self._ck(self._L.rbf_last_step_timing(self._h, ctypes.byref(t), ctypes.byref(k), ctypes.byref(n)))
+        return t.value, k.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self._L.rbf_launch_count(self._h))

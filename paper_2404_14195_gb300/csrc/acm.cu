@@ -1,0 +1,189 @@
+// acm.cu — explicit artificial-compressibility Navier-Stokes step (MNS section,
+// Eqs. MNS_intermediate, MNS_pressure, MNS_velocity, MNS_C; MNS algorithm of the
+// appendix), one thread per node in SELL-C slices of 32 Morton-ordered nodes.
+//
+// Per step:   predict  v' = v + dt (nu lap v - (v . grad) v + g)   fluid; v' = 0 walls
+//             n_p x {  pressure  p -= dt C^2 rho div v            fluid
+//                      wall p from n . grad p = 0 on the Neumann stencil
+//                      correct   v = v' - dt/rho grad p           fluid; 0 walls
+//                                C = beta max(max |v|, v_ref)  }
+// Stencil gathers read u, v, w, p at the neighbour indices; weights stream from
+// HBM as SELL slices [slice][operator][j][lane] (coalesced 128-byte rows).
+// max |v| is reduced per block with warp shuffles and merged with one 64-bit
+// atomicMax per block into one of two ping-pong slots (non-negative IEEE values
+// order like their bit patterns), which the next pressure sweep reads.
+#include "acm.cuh"
+
+namespace rbf {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_acm_predict(AcmArgs<T> a) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    if (a.type[i]) {
+        a.us[i] = (T)0; a.vs[i] = (T)0; a.ws[i] = (T)0;
+        return;
+    }
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int n_l = a.n_l;
+    const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
+    const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
+    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+    for (int j = 0; j < n_l; ++j) {
+        int q = __ldg(ip + (j << 5));
+        T wx = __ldg(wp + (j << 5)), wy = __ldg(wp + ((n_l + j) << 5));
+        T wz = __ldg(wp + ((2 * n_l + j) << 5)), wl = __ldg(wp + ((3 * n_l + j) << 5));
+        T uq = a.u[q], vq = a.v[q], wq = a.w_[q];
+        gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
+        gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
+        gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
+    }
+    T ui = a.u[i], vi = a.v[i], wi = a.w_[i];
+    T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
+    T adv_v = ui * gv[0] + vi * gv[1] + wi * gv[2];
+    T adv_w = ui * gw[0] + vi * gw[1] + wi * gw[2];
+    a.us[i] = ui + a.dt * (a.nu * gu[3] - adv_u + a.gx);
+    a.vs[i] = vi + a.dt * (a.nu * gv[3] - adv_v + a.gy);
+    a.ws[i] = wi + a.dt * (a.nu * gw[3] - adv_w + a.gz);
+}
+
+// speed of sound of Eq. MNS_C from the max |v| stored (as double bits) in a slot
+__device__ __forceinline__ double acm_C(const unsigned long long *slot, double beta, double vref) {
+    double vmax = __longlong_as_double((long long)*slot);
+    return beta * (vmax > vref ? vmax : vref);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__restrict__ u, const T *__restrict__ v,
+                                                     const T *__restrict__ w, int read_slot, int zero_slot) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) a.vmax[zero_slot] = 0ULL;
+    if (i >= a.n || a.type[i]) return;
+    const double C = acm_C(a.vmax + read_slot, a.beta, a.vref);
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int n_l = a.n_l;
+    const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
+    const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
+    T div = 0;
+    for (int j = 0; j < n_l; ++j) {
+        int q = __ldg(ip + (j << 5));
+        T wx = __ldg(wp + (j << 5)), wy = __ldg(wp + ((n_l + j) << 5)), wz = __ldg(wp + ((2 * n_l + j) << 5));
+        div += wx * u[q] + wy * v[q] + wz * w[q];
+    }
+    const T Ct = (T)C;
+    a.p[i] = a.p[i] - a.dt * Ct * Ct * a.rho * div;
+}
+
+// wall pressure from the Neumann condition, on the wall nodes' own stencils
+// {b, nearest fluid nodes}: p_b = -sum_{j>=1} w^n_j p_j / w^n_0
+template <typename T>
+__global__ void __launch_bounds__(256) k_acm_wall_pressure(AcmArgs<T> a) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= a.nb) return;
+    const int64_t s = b >> 5;
+    const int lane = (int)(b & 31);
+    const int n_l = a.n_l;
+    const int32_t *__restrict__ ip = a.idxb + ((s * n_l) << 5) + lane;
+    const T *__restrict__ wp = a.wn + ((s * n_l) << 5) + lane;
+    T acc = 0;
+    for (int j = 1; j < n_l; ++j) acc += __ldg(wp + (j << 5)) * a.p[__ldg(ip + (j << 5))];
+    a.p[a.wall[b]] = -acc / __ldg(wp);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slot) {
+    __shared__ double red[8];
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double speed = 0.0;
+    if (i < a.n) {
+        if (a.type[i]) {
+            a.u[i] = (T)0; a.v[i] = (T)0; a.w_[i] = (T)0;
+        } else {
+            const int64_t s = i >> 5;
+            const int lane = (int)(i & 31);
+            const int n_l = a.n_l;
+            const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
+            const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
+            T gx = 0, gy = 0, gz = 0;
+            for (int j = 0; j < n_l; ++j) {
+                T pq = a.p[__ldg(ip + (j << 5))];
+                gx += __ldg(wp + (j << 5)) * pq;
+                gy += __ldg(wp + ((n_l + j) << 5)) * pq;
+                gz += __ldg(wp + ((2 * n_l + j) << 5)) * pq;
+            }
+            const T f = a.dt / a.rho;
+            T un = a.us[i] - f * gx, vn = a.vs[i] - f * gy, wn = a.ws[i] - f * gz;
+            a.u[i] = un; a.v[i] = vn; a.w_[i] = wn;
+            speed = (double)sqrt(un * un + vn * vn + wn * wn);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) speed = fmax(speed, __shfl_xor_sync(0xffffffffu, speed, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = speed;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0 && v > 0.0) atomicMax(a.vmax + write_slot, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// max |v| of the current field into a slot (initial C)
+template <typename T>
+__global__ void k_acm_vmax(AcmArgs<T> a, int slot) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double sp = 0.0;
+    if (i < a.n) sp = (double)sqrt(a.u[i] * a.u[i] + a.v[i] * a.v[i] + a.w_[i] * a.w_[i]);
+    for (int off = 16; off > 0; off >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, off));
+    if ((threadIdx.x & 31) == 0 && sp > 0.0) atomicMax(a.vmax + slot, (unsigned long long)__double_as_longlong(sp));
+}
+
+// Iteration g of the run (counted over all steps) writes max |v| into slot g % 2;
+// the pressure sweep of iteration g reads slot (g + 1) % 2 (the previous
+// iteration's) and clears slot g % 2 for its own correction sweep.
+template <typename T>
+cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches) {
+    const unsigned gb = (unsigned)((a.n + 255) / 256);
+    const unsigned gw = (unsigned)((a.nb + 255) / 256);
+    k_acm_predict<T><<<gb, 256, 0, st>>>(a);
+    ++*launches;
+    for (int it = 0; it < n_p; ++it) {
+        const T *u = it == 0 ? a.us : a.u;
+        const T *v = it == 0 ? a.vs : a.v;
+        const T *w = it == 0 ? a.ws : a.w_;
+        const int g = (parity + it) & 1;
+        k_acm_pressure<T><<<gb, 256, 0, st>>>(a, u, v, w, g ^ 1, g);
+        ++*launches;
+        if (a.nb > 0) {
+            k_acm_wall_pressure<T><<<gw, 256, 0, st>>>(a);
+            ++*launches;
+        }
+        k_acm_correct<T><<<gb, 256, 0, st>>>(a, g);
+        ++*launches;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(a.vmax + slot, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_acm_vmax<T><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a, slot);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t acm_launch_predict_only(const AcmArgs<T> &a, cudaStream_t st) {
+    k_acm_predict<T><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t acm_launch_step<float>(const AcmArgs<float> &, int, int, cudaStream_t, int64_t *);
+template cudaError_t acm_launch_step<double>(const AcmArgs<double> &, int, int, cudaStream_t, int64_t *);
+template cudaError_t acm_launch_vmax<float>(const AcmArgs<float> &, int, cudaStream_t);
+template cudaError_t acm_launch_vmax<double>(const AcmArgs<double> &, int, cudaStream_t);
+template cudaError_t acm_launch_predict_only<float>(const AcmArgs<float> &, cudaStream_t);
+template cudaError_t acm_launch_predict_only<double>(const AcmArgs<double> &, cudaStream_t);
+
+}  // namespace rbf

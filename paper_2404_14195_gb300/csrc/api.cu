@@ -1,0 +1,939 @@
+// api.cu — the C ABI of include/rbfgb.h: device-resident state of one case and
+// the host-side orchestration of the kernels (node ordering, stencils, weights,
+// time stepping with CUDA graphs, reductions).  No arithmetic of the method
+// runs on the host; host code validates arguments, sizes buffers and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rbfgb.h"
+#include "acm.cuh"
+#include "internal.cuh"
+#include "lbm.cuh"
+#include "reduce.cuh"
+
+using namespace rbf;
+
+namespace {
+
+template <typename T>
+struct DevArr {
+    T *p = nullptr;
+    size_t n = 0;
+    DevArr() = default;
+    DevArr(const DevArr &) = delete;
+    DevArr &operator=(const DevArr &) = delete;
+    ~DevArr() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t m) {
+        release();
+        if (m == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc((void **)&p, m * sizeof(T));
+        if (e == cudaSuccess) n = m; else p = nullptr;
+        return e;
+    }
+    cudaError_t zero(cudaStream_t st) { return n ? cudaMemsetAsync(p, 0, n * sizeof(T), st) : cudaSuccess; }
+};
+
+}  // namespace
+
+struct rbf_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int64_t launches = 0;
+    // nodes (device arrays in Morton order)
+    int64_t n = 0, npad = 0, nb = 0, nf = 0;
+    DevArr<double> xyz, nrm;
+    DevArr<uint8_t> type;
+    DevArr<int32_t> perm, iperm, wall, iota;
+    bool has_sphere = false;
+    double c[3] = {0.5, 0.5, 0.5}, r = 0.0;
+    // stencils
+    int G = 0, n_l = 0;
+    DevArr<int32_t> cstart, citems, idx, idxb, idxw, idx_sell, idxb_sell;
+    // weights
+    bool weights_ok = false;
+    int solver = -1, q = 0, phs_k = 0, mono_m = 0, n_ops = 0;
+    double dx = 0.0, h_min = 0.0;
+    DevArr<double> w64, wgb64, wgw64, delta;
+    DevArr<float> ws32, wn32;
+    DevArr<double> ws64, wn64;
+    DevArr<uint32_t> mask;
+    // fields
+    bool inited = false;
+    int prec = RBF_FP64;
+    rbf_params prm{};
+    double dt = 0.0, vref = 0.0, beta = 10.0, rho = 1.0;
+    int n_p = 3, parity = 0;
+    DevArr<float> a32[10];
+    DevArr<double> a64[10];
+    DevArr<unsigned long long> vmax;
+    double tp = 0.8, tm = 1.125, gl[3] = {0, 0, 0}, lbm_dt = 0.0;
+    DevArr<float> f32[2];
+    DevArr<double> f64[2];
+    int cur = 0;
+    // probes
+    int m_p = 0;
+    int64_t np_fluid = 0;
+    DevArr<double> pxyz, pw;
+    DevArr<int32_t> pidx;
+    // scratch
+    DevArr<double> partial, scal, mac, hostbuf_dev;
+    DevArr<int32_t> status;
+    // graph of `gsteps` steps
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0, gparity = -1, gcur = -1, gprec = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = 0.0;
+    int64_t last_steps = 0;
+    int64_t last_kernel_launches = 0;
+};
+
+namespace {
+
+int fail(rbf_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+int cuda_fail(rbf_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? RBF_ENOMEM : RBF_ECUDA, m);
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);    \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+void drop_graph(rbf_ctx *ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gsteps = 0;
+}
+
+int binom(int a, int b) {
+    long r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return (int)r;
+}
+
+double porosity_of(double r) {
+    double v = 4.0 / 3.0 * M_PI * r * r * r;
+    if (r > 0.5) {
+        double h = r - 0.5;
+        v -= 6.0 * M_PI * h * h * (3.0 * r - h) / 3.0;
+    }
+    return 1.0 - v;
+}
+double wall_area_of(double r) {
+    double a = 4.0 * M_PI * r * r;
+    if (r > 0.5) a -= 6.0 * 2.0 * M_PI * r * (r - 0.5);
+    return a;
+}
+
+__global__ void k_iota(int32_t *a, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
+}
+__global__ void k_gather_rows(int64_t nr, int n_l, const int32_t *rows, const int32_t *idx, int32_t *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nr * n_l) return;
+    int64_t r = t / n_l;
+    int j = (int)(t - r * n_l);
+    out[t] = idx[(int64_t)rows[r] * n_l + j];
+}
+__global__ void k_gather_wrows(int64_t nr, int n_l, int n_ops, const int32_t *rows, const double *w, double *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nr * 3 * n_l) return;
+    int64_t r = t / (3 * n_l);
+    int rem = (int)(t - r * 3 * n_l);
+    out[t] = w[(int64_t)rows[r] * n_ops * n_l + rem];
+}
+// probe points on the five planes x = 0, .2, .4, .6, .8; flag = fluid (outside every
+// periodic image of the sphere)
+__global__ void k_probe_points(int m_p, double cx, double cy, double cz, double r, int has_sphere, double *pts,
+                               int32_t *flag) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tot = 5LL * m_p * m_p;
+    if (t >= tot) return;
+    int pl = (int)(t / ((int64_t)m_p * m_p));
+    int rem = (int)(t - (int64_t)pl * m_p * m_p);
+    int a = rem / m_p, b = rem - a * m_p;
+    double x = 0.2 * pl, y = (a + 0.5) / m_p, z = (b + 0.5) / m_p;
+    pts[3 * t] = x; pts[3 * t + 1] = y; pts[3 * t + 2] = z;
+    int fl = 1;
+    if (has_sphere) {
+        double dx = mimg(x - cx), dy = mimg(y - cy), dz = mimg(z - cz);
+        fl = sqrt(dx * dx + dy * dy + dz * dz) - r >= 0.0;
+    }
+    flag[t] = fl;
+}
+__global__ void k_probe_compact(int64_t tot, const double *pts, const int32_t *flag, const int32_t *scan, double *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= tot || !flag[t]) return;
+    int64_t o = scan[t];
+    out[3 * o] = pts[3 * t]; out[3 * o + 1] = pts[3 * t + 1]; out[3 * o + 2] = pts[3 * t + 2];
+}
+
+unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+AcmArgs<T> acm_args(rbf_ctx *ctx, DevArr<T> *a, const DevArr<T> &ws, const DevArr<T> &wn) {
+    AcmArgs<T> g;
+    g.n = ctx->n; g.nb = ctx->nb; g.n_l = ctx->n_l;
+    g.idx = ctx->idx_sell.p; g.w = ws.p; g.type = ctx->type.p; g.wall = ctx->wall.p;
+    g.idxb = ctx->idxb_sell.p; g.wn = wn.p;
+    g.u = a[0].p; g.v = a[1].p; g.w_ = a[2].p; g.p = a[3].p;
+    g.us = a[4].p; g.vs = a[5].p; g.ws = a[6].p;
+    g.vmax = ctx->vmax.p;
+    g.dt = (T)ctx->dt; g.nu = (T)ctx->prm.nu;
+    g.gx = (T)ctx->prm.g[0]; g.gy = (T)ctx->prm.g[1]; g.gz = (T)ctx->prm.g[2];
+    g.rho = (T)ctx->rho; g.beta = ctx->beta; g.vref = ctx->vref;
+    return g;
+}
+
+template <typename T>
+LbmArgs<T> lbm_args(rbf_ctx *ctx, DevArr<T> *f, const DevArr<T> &ws, int cur) {
+    LbmArgs<T> g;
+    g.n = ctx->n; g.npad = ctx->npad; g.n_l = ctx->n_l;
+    g.idx = ctx->idx_sell.p; g.w = ws.p; g.mask = ctx->mask.p;
+    g.fin = f[cur].p; g.fout = f[cur ^ 1].p;
+    g.tp_inv = (T)(1.0 / ctx->tp); g.tm_inv = (T)(1.0 / ctx->tm);
+    g.gx = (T)ctx->gl[0]; g.gy = (T)ctx->gl[1]; g.gz = (T)ctx->gl[2];
+    return g;
+}
+
+// enqueue `steps` steps starting from (parity, cur); updates them
+cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_t *launches) {
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+        if (ctx->solver == RBF_SOLVER_ACM) {
+            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches);
+            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches);
+            parity = (parity + ctx->n_p) & 1;
+        } else {
+            if (ctx->prec == RBF_FP32) e = lbm_launch_step<float>(lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur), ctx->q, ctx->st);
+            else e = lbm_launch_step<double>(lbm_args<double>(ctx, ctx->f64, ctx->ws64, cur), ctx->q, ctx->st);
+            ++*launches;
+            cur ^= 1;
+        }
+    }
+    return e;
+}
+
+int run_steps(rbf_ctx *ctx, int64_t nsteps) {
+    const int chunk = ctx->solver == RBF_SOLVER_ACM ? 16 : 32;  // even: parity / buffer return to start
+    int64_t full = nsteps / chunk, rem = nsteps % chunk;
+    int64_t kl = 0;
+    if (full > 0) {
+        if (!ctx->gexec || ctx->gparity != ctx->parity || ctx->gcur != ctx->cur || ctx->gprec != ctx->prec ||
+            ctx->gsteps != chunk) {
+            drop_graph(ctx);
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+            int par = ctx->parity, cu = ctx->cur;
+            int64_t dummy = 0;
+            cudaError_t e = enqueue_steps(ctx, chunk, par, cu, &dummy);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->st, &g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "capture");
+            if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+            ctx->gsteps = chunk;
+            ctx->gparity = ctx->parity;
+            ctx->gcur = ctx->cur;
+            ctx->gprec = ctx->prec;
+            ctx->last_kernel_launches = dummy;
+        }
+        int64_t per_graph = ctx->last_kernel_launches;
+        for (int64_t r = 0; r < full; ++r) {
+            CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+            kl += per_graph;
+        }
+    }
+    if (rem > 0) {
+        cudaError_t e = enqueue_steps(ctx, (int)rem, ctx->parity, ctx->cur, &kl);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+    }
+    ctx->launches += kl;
+    return RBF_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int rbf_create(rbf_ctx **out, int device, void *cuda_stream) {
+    if (!out) return RBF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0 || device < 0 || device >= ndev) return RBF_ECUDA;
+    rbf_ctx *ctx = new rbf_ctx();
+    ctx->device = device;
+    DeviceGuard dg(device);
+    if (cuda_stream) {
+        ctx->st = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return RBF_ECUDA; }
+        ctx->own_stream = true;
+    }
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        ctx->vmax.alloc(2) != cudaSuccess || ctx->scal.alloc(16) != cudaSuccess || ctx->status.alloc(4) != cudaSuccess) {
+        rbf_destroy(ctx);
+        return RBF_ECUDA;
+    }
+    *out = ctx;
+    return RBF_OK;
+}
+
+int rbf_destroy(rbf_ctx *ctx) {
+    if (!ctx) return RBF_EINVAL;
+    {
+        DeviceGuard dg(ctx->device);
+        if (ctx->st) cudaStreamSynchronize(ctx->st);
+        drop_graph(ctx);
+        if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+        if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+        if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+        ctx->st = nullptr;
+    }
+    {
+        DeviceGuard dg(ctx->device);
+        delete ctx;  // DevArr destructors free device memory on this device
+    }
+    return RBF_OK;
+}
+
+const char *rbf_last_error(const rbf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t rbf_launch_count(const rbf_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int rbf_set_nodes(rbf_ctx *ctx, int64_t n, const double *xyz, const uint8_t *type, const double *normal) {
+    if (!ctx) return RBF_EINVAL;
+    if (n < 2 || n > (int64_t)INT32_MAX / 64 || !xyz || !type) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: bad n or null array");
+    int64_t nb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double x = xyz[3 * i + a];
+            if (!(x >= 0.0 && x <= 1.0)) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: coordinates must lie in [0, 1]");
+        }
+        if (type[i] > 1) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: type must be 0 (fluid) or 1 (wall)");
+        if (type[i]) {
+            if (!normal) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: wall nodes need normals");
+            double l = std::sqrt(normal[3 * i] * normal[3 * i] + normal[3 * i + 1] * normal[3 * i + 1] +
+                                 normal[3 * i + 2] * normal[3 * i + 2]);
+            if (!(std::fabs(l - 1.0) < 1e-6)) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: wall normals must be unit");
+            ++nb;
+        }
+    }
+    DeviceGuard dg(ctx->device);
+    CK(cudaStreamSynchronize(ctx->st));
+    drop_graph(ctx);
+    ctx->weights_ok = false;
+    ctx->inited = false;
+    ctx->n_l = 0;
+    ctx->m_p = 0;
+    ctx->n = n;
+    ctx->npad = (n + 31) & ~31LL;
+    ctx->nb = nb;
+    ctx->nf = n - nb;
+    int64_t npow = 1;
+    while (npow < n) npow <<= 1;
+    DevArr<double> xyz0, nrm0;
+    DevArr<uint8_t> type0;
+    DevArr<uint64_t> keys;
+    DevArr<int32_t> vals;
+    CK(xyz0.alloc(3 * n)); CK(nrm0.alloc(3 * n)); CK(type0.alloc(n));
+    CK(keys.alloc(npow)); CK(vals.alloc(npow));
+    CK(cudaMemcpyAsync(xyz0.p, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(type0.p, type, n, cudaMemcpyHostToDevice, ctx->st));
+    if (normal) CK(cudaMemcpyAsync(nrm0.p, normal, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    else CK(nrm0.zero(ctx->st));
+    CK(launch_morton_keys(n, xyz0.p, keys.p, vals.p, npow, ctx->st));
+    ++ctx->launches;
+    CK(launch_bitonic_sort(keys.p, vals.p, npow, ctx->st, &ctx->launches));
+    CK(ctx->xyz.alloc(3 * n)); CK(ctx->nrm.alloc(3 * n)); CK(ctx->type.alloc(n));
+    CK(ctx->perm.alloc(n)); CK(ctx->iperm.alloc(n)); CK(ctx->iota.alloc(n));
+    CK(cudaMemcpyAsync(ctx->perm.p, vals.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(launch_gather_nodes(n, ctx->perm.p, xyz0.p, type0.p, nrm0.p, ctx->xyz.p, ctx->type.p, ctx->nrm.p,
+                           ctx->iperm.p, ctx->st));
+    k_iota<<<nblk(n), 256, 0, ctx->st>>>(ctx->iota.p, n);
+    ctx->launches += 2;
+    // wall list (sorted order)
+    CK(ctx->wall.alloc(nb));
+    if (nb > 0) {
+        DevArr<int32_t> flags, scan, tmp;
+        CK(flags.alloc(n)); CK(scan.alloc(n)); CK(tmp.alloc(scan_tmp_len(n)));
+        CK(launch_type_flags(n, ctx->type.p, 1, flags.p, ctx->st));
+        CK(launch_scan_i32(flags.p, scan.p, n, tmp.p, tmp.n, ctx->st, &ctx->launches));
+        CK(launch_flag_compact(n, ctx->type.p, 1, scan.p, ctx->wall.p, ctx->st));
+        ctx->launches += 2;
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaGetLastError());
+    return RBF_OK;
+}
+
+int rbf_set_sphere(rbf_ctx *ctx, const double c[3], double r) {
+    if (!ctx || !c) return RBF_EINVAL;
+    if (!(r > 0.0 && r < 0.7071)) return fail(ctx, RBF_EINVAL, "rbf_set_sphere: r must lie in (0, sqrt(2)/2)");
+    for (int a = 0; a < 3; ++a) ctx->c[a] = c[a];
+    ctx->r = r;
+    ctx->has_sphere = true;
+    ctx->m_p = 0;
+    return RBF_OK;
+}
+
+int rbf_build_stencils(rbf_ctx *ctx, int n_l) {
+    if (!ctx) return RBF_EINVAL;
+    if (ctx->n == 0) return fail(ctx, RBF_EINVAL, "rbf_build_stencils: no nodes");
+    if (n_l < 2 || n_l > RBF_MAX_NL || n_l > ctx->n) return fail(ctx, RBF_EINVAL, "rbf_build_stencils: need 2 <= n_l <= min(64, n)");
+    if (ctx->nb > 0 && ctx->nf < n_l - 1) return fail(ctx, RBF_EINVAL, "rbf_build_stencils: too few fluid nodes for the wall stencils");
+    DeviceGuard dg(ctx->device);
+    drop_graph(ctx);
+    ctx->weights_ok = false;
+    ctx->inited = false;
+    ctx->m_p = 0;
+    const int64_t n = ctx->n;
+    int G = (int)std::lround(std::cbrt((double)n / 4.0));
+    G = std::max(1, std::min(G, 400));
+    ctx->G = G;
+    const int64_t ncell = (int64_t)G * G * G;
+    DevArr<int32_t> cell_of, counts, fill, tmp;
+    CK(cell_of.alloc(n)); CK(counts.alloc(ncell + 1)); CK(fill.alloc(ncell));
+    CK(ctx->cstart.alloc(ncell + 1)); CK(ctx->citems.alloc(n)); CK(tmp.alloc(scan_tmp_len(ncell + 1)));
+    CK(counts.zero(ctx->st)); CK(fill.zero(ctx->st));
+    CK(launch_cell_count(n, ctx->xyz.p, G, cell_of.p, counts.p, ctx->st));
+    CK(launch_scan_i32(counts.p, ctx->cstart.p, ncell + 1, tmp.p, tmp.n, ctx->st, &ctx->launches));
+    CK(launch_cell_fill(n, cell_of.p, ctx->cstart.p, fill.p, ctx->citems.p, ctx->st));
+    ctx->launches += 2;
+    CK(ctx->idx.alloc(n * n_l));
+    CK(ctx->status.zero(ctx->st));
+    CK(launch_knn(n, nullptr, ctx->iota.p, ctx->xyz.p, ctx->perm.p, ctx->type.p, 0, G, ctx->cstart.p,
+                  ctx->citems.p, n_l, ctx->idx.p, n_l, 0, ctx->status.p, ctx->st));
+    ++ctx->launches;
+    CK(ctx->idxb.alloc(ctx->nb * n_l));
+    CK(ctx->idxw.alloc(ctx->nb * n_l));
+    if (ctx->nb > 0) {
+        CK(cudaMemcpy2DAsync(ctx->idxb.p, n_l * sizeof(int32_t), ctx->wall.p, sizeof(int32_t), sizeof(int32_t),
+                             ctx->nb, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(launch_knn(ctx->nb, nullptr, ctx->wall.p, ctx->xyz.p, ctx->perm.p, ctx->type.p, 1, G, ctx->cstart.p,
+                      ctx->citems.p, n_l - 1, ctx->idxb.p, n_l, 1, ctx->status.p, ctx->st));
+        k_gather_rows<<<nblk(ctx->nb * n_l), 256, 0, ctx->st>>>(ctx->nb, n_l, ctx->wall.p, ctx->idx.p, ctx->idxw.p);
+        ctx->launches += 2;
+    }
+    int32_t stat = 0;
+    CK(cudaMemcpyAsync(&stat, ctx->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (stat) return fail(ctx, RBF_EINVAL, "rbf_build_stencils: not enough candidate nodes");
+    CK(ctx->idx_sell.alloc(ctx->npad * n_l));
+    CK(launch_pack_idx(n, n_l, ctx->idx.p, ctx->idx_sell.p, ctx->st));
+    CK(ctx->idxb_sell.alloc(((ctx->nb + 31) & ~31LL) * n_l));
+    CK(launch_pack_idx(ctx->nb, n_l, ctx->idxb.p, ctx->idxb_sell.p, ctx->st));
+    ctx->launches += 2;
+    ctx->n_l = n_l;
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_get_stencils(rbf_ctx *ctx, int32_t *idx) {
+    if (!ctx || !idx) return RBF_EINVAL;
+    if (!ctx->n_l) return fail(ctx, RBF_EINVAL, "rbf_get_stencils: no stencils");
+    DeviceGuard dg(ctx->device);
+    DevArr<int32_t> out;
+    CK(out.alloc(ctx->n * ctx->n_l));
+    CK(launch_export_stencils(ctx->n, ctx->n_l, ctx->perm.p, ctx->iperm.p, ctx->idx.p, out.p, ctx->st));
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(idx, out.p, out.n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, double dx, rbf_weight_report *rep) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->n_l) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: build stencils first");
+    if (phs_k < 3 || phs_k % 2 == 0 || phs_k > 9) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: phs_k must be odd, 3..9");
+    if (mono_m < 0 || mono_m > 4) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: mono_m must lie in 0..4");
+    const int np = binom(mono_m + 3, 3);
+    if (ctx->n_l < np) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: n_l < N_p");
+    if (solver != RBF_SOLVER_ACM && solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: bad solver");
+    if (solver == RBF_SOLVER_LBM && (q != 15 && q != 19)) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: q must be 15 or 19");
+    if (solver == RBF_SOLVER_LBM && !(dx > 0.0 && dx < 0.25)) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: bad dx");
+    DeviceGuard dg(ctx->device);
+    drop_graph(ctx);
+    ctx->weights_ok = false;
+    ctx->inited = false;
+    const int64_t n = ctx->n, nb = ctx->nb;
+    const int n_l = ctx->n_l;
+    std::vector<OpSpec> ops;
+    if (solver == RBF_SOLVER_ACM) {
+        for (int kind : {OP_DX, OP_DY, OP_DZ, OP_LAP}) ops.push_back(OpSpec{kind, {0.0, 0.0, 0.0}});
+    } else {
+        const int *e = host_velocity_set(q);
+        for (int k = 1; k < q; ++k)
+            ops.push_back(OpSpec{OP_INTERP, {-dx * e[3 * k], -dx * e[3 * k + 1], -dx * e[3 * k + 2]}});
+    }
+    std::vector<OpSpec> gops;
+    for (int kind : {OP_DX, OP_DY, OP_DZ}) gops.push_back(OpSpec{kind, {0.0, 0.0, 0.0}});
+    const int n_ops = (int)ops.size();
+    DevArr<OpSpec> d_ops, d_gops;
+    CK(d_ops.alloc(ops.size())); CK(d_gops.alloc(3));
+    CK(cudaMemcpyAsync(d_ops.p, ops.data(), ops.size() * sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(d_gops.p, gops.data(), 3 * sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
+    CK(ctx->w64.alloc(n * n_ops * n_l));
+    CK(ctx->delta.alloc(n));
+    CK(ctx->status.zero(ctx->st));
+    CK(launch_weights(n, ctx->xyz.p, nullptr, ctx->iota.p, 1, n_l, ctx->idx.p, phs_k, mono_m, n_ops, d_ops.p, 1,
+                      ctx->w64.p, ctx->delta.p, ctx->status.p, ctx->st));
+    ++ctx->launches;
+    CK(ctx->wgw64.alloc(nb * 3 * n_l));
+    CK(ctx->wgb64.alloc(nb * 3 * n_l));
+    if (nb > 0) {
+        if (solver == RBF_SOLVER_ACM) {
+            k_gather_wrows<<<nblk(nb * 3 * n_l), 256, 0, ctx->st>>>(nb, n_l, 4, ctx->wall.p, ctx->w64.p, ctx->wgw64.p);
+            ++ctx->launches;
+            CK(launch_weights(nb, ctx->xyz.p, nullptr, ctx->wall.p, 1, n_l, ctx->idxb.p, phs_k, mono_m, 3, d_gops.p, 1,
+                              ctx->wgb64.p, nullptr, ctx->status.p + 1, ctx->st));
+        } else {
+            CK(launch_weights(nb, ctx->xyz.p, nullptr, ctx->wall.p, 1, n_l, ctx->idxw.p, phs_k, mono_m, 3, d_gops.p, 1,
+                              ctx->wgw64.p, nullptr, ctx->status.p + 1, ctx->st));
+        }
+        ++ctx->launches;
+    }
+    if (ctx->partial.n < (size_t)(4 * (nblk(n) + 8))) CK(ctx->partial.alloc(4 * (nblk(n) + 8)));
+    CK(launch_min_f64(ctx->delta.p, n, ctx->partial.p, ctx->scal.p, ctx->st));
+    ctx->launches += 2;
+    int32_t sing[2] = {0, 0};
+    double hmin = 0.0;
+    CK(cudaMemcpyAsync(sing, ctx->status.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(&hmin, ctx->scal.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    // SELL packs in both precisions
+    const int n_out = n_ops;
+    CK(ctx->ws32.alloc(ctx->npad * n_out * n_l));
+    CK(ctx->ws64.alloc(ctx->npad * n_out * n_l));
+    CK(launch_pack_f32(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
+    CK(launch_pack_f64(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+    ctx->launches += 2;
+    const int64_t nbpad = (nb + 31) & ~31LL;
+    if (solver == RBF_SOLVER_ACM) {
+        CK(ctx->wn32.alloc(nbpad * n_l));
+        CK(ctx->wn64.alloc(nbpad * n_l));
+        CK(launch_pack_normal_f32(nb, n_l, ctx->wall.p, ctx->nrm.p, ctx->wgb64.p, ctx->wn32.p, ctx->st));
+        CK(launch_pack_normal_f64(nb, n_l, ctx->wall.p, ctx->nrm.p, ctx->wgb64.p, ctx->wn64.p, ctx->st));
+        ctx->launches += 2;
+        ctx->mask.release();
+    } else {
+        ctx->wn32.release();
+        ctx->wn64.release();
+        CK(ctx->mask.alloc(n));
+        CK(lbm_launch_masks(n, q, ctx->type.p, ctx->nrm.p, ctx->mask.p, ctx->st));
+        ++ctx->launches;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->solver = solver;
+    ctx->q = solver == RBF_SOLVER_LBM ? q : 0;
+    ctx->dx = dx;
+    ctx->phs_k = phs_k;
+    ctx->mono_m = mono_m;
+    ctx->n_ops = n_ops;
+    ctx->h_min = hmin;
+    ctx->m_p = 0;
+    if (rep) {
+        rep->n_systems = n + nb;
+        rep->n_singular = sing[0] + sing[1];
+        rep->h_min = hmin;
+    }
+    if (sing[0] + sing[1] > 0) return fail(ctx, RBF_ESINGULAR, "rbf_compute_weights: singular stencil systems");
+    ctx->weights_ok = true;
+    return RBF_OK;
+}
+
+int rbf_get_weights(rbf_ctx *ctx, int op, double *out) {
+    if (!ctx || !out) return RBF_EINVAL;
+    if (!ctx->weights_ok) return fail(ctx, RBF_EINVAL, "rbf_get_weights: no weights");
+    int o;
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        if (op < RBF_OP_DX || op > RBF_OP_LAP) return fail(ctx, RBF_EINVAL, "rbf_get_weights: bad op for ACM");
+        o = op;
+    } else {
+        o = op - RBF_OP_LBM0 - 1;
+        if (o < 0 || o >= ctx->q - 1) return fail(ctx, RBF_EINVAL, "rbf_get_weights: bad op for LBM");
+    }
+    DeviceGuard dg(ctx->device);
+    DevArr<double> d;
+    CK(d.alloc(ctx->n * ctx->n_l));
+    CK(launch_export_weights(ctx->n, ctx->n_l, ctx->n_ops, o, ctx->iperm.p, nullptr, ctx->w64.p, d.p, ctx->st));
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(out, d.p, d.n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
+    if (!ctx || !p) return RBF_EINVAL;
+    if (!ctx->weights_ok) return fail(ctx, RBF_EINVAL, "rbf_init: compute weights first");
+    if (p->precision != RBF_FP32 && p->precision != RBF_FP64) return fail(ctx, RBF_EINVAL, "rbf_init: bad precision");
+    if (!(p->nu > 0.0)) return fail(ctx, RBF_EINVAL, "rbf_init: nu must be > 0");
+    DeviceGuard dg(ctx->device);
+    CK(cudaStreamSynchronize(ctx->st));
+    drop_graph(ctx);
+    ctx->prm = *p;
+    ctx->prec = p->precision;
+    ctx->rho = p->rho > 0.0 ? p->rho : 1.0;
+    ctx->prm.rho = ctx->rho;
+    const double gmag = std::sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
+    const int64_t n = ctx->n, npad = ctx->npad;
+    for (auto &a : ctx->a32) a.release();
+    for (auto &a : ctx->a64) a.release();
+    for (auto &a : ctx->f32) a.release();
+    for (auto &a : ctx->f64) a.release();
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        const double cfl = p->cfl > 0.0 ? p->cfl : 0.1;
+        ctx->dt = p->dt > 0.0 ? p->dt : cfl * ctx->h_min * ctx->h_min / (2.0 * p->nu);
+        ctx->beta = p->beta > 0.0 ? p->beta : 10.0;
+        ctx->vref = p->v_ref > 0.0 ? p->v_ref : 0.01 * gmag / p->nu;
+        ctx->n_p = p->n_p > 0 ? p->n_p : 3;
+        ctx->parity = 0;
+        for (int a = 0; a < 10; ++a) {
+            if (ctx->prec == RBF_FP32) { CK(ctx->a32[a].alloc(npad)); CK(ctx->a32[a].zero(ctx->st)); }
+            else { CK(ctx->a64[a].alloc(npad)); CK(ctx->a64[a].zero(ctx->st)); }
+        }
+        CK(ctx->vmax.zero(ctx->st));  // v = 0: max |v| = 0, C = beta v_ref
+    } else {
+        ctx->tp = p->tau_plus > 0.5 ? p->tau_plus : 0.8;
+        const double magic = p->magic > 0.0 ? p->magic : 3.0 / 16.0;
+        ctx->tm = 0.5 + magic / (ctx->tp - 0.5);
+        const double nu_lb = (ctx->tp - 0.5) / 3.0;
+        ctx->lbm_dt = nu_lb * ctx->dx * ctx->dx / p->nu;
+        ctx->dt = ctx->lbm_dt;
+        for (int a = 0; a < 3; ++a) ctx->gl[a] = p->g[a] * ctx->lbm_dt * ctx->lbm_dt / ctx->dx;
+        ctx->cur = 0;
+        const int64_t sz = (int64_t)ctx->q * npad;
+        if (ctx->prec == RBF_FP32) {
+            CK(ctx->f32[0].alloc(sz)); CK(ctx->f32[1].alloc(sz)); CK(ctx->f32[1].zero(ctx->st));
+            LbmArgs<float> a = lbm_args<float>(ctx, ctx->f32, ctx->ws32, 1);  // writes f32[0]
+            CK(lbm_launch_init<float>(a, ctx->q, ctx->st));
+        } else {
+            CK(ctx->f64[0].alloc(sz)); CK(ctx->f64[1].alloc(sz)); CK(ctx->f64[1].zero(ctx->st));
+            LbmArgs<double> a = lbm_args<double>(ctx, ctx->f64, ctx->ws64, 1);
+            CK(lbm_launch_init<double>(a, ctx->q, ctx->st));
+        }
+        ++ctx->launches;
+    }
+    CK(ctx->mac.alloc(4 * n));
+    {
+        const size_t need = (size_t)(4 * (std::max<int64_t>(n, 5LL * 512 * 512) / 256 + 8));
+        if (ctx->partial.n < need) CK(ctx->partial.alloc(need));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->inited = true;
+    return RBF_OK;
+}
+
+int rbf_step(rbf_ctx *ctx, int nsteps) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_step: call rbf_init first");
+    if (nsteps < 0) return fail(ctx, RBF_EINVAL, "rbf_step: nsteps < 0");
+    DeviceGuard dg(ctx->device);
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
+    int rc = run_steps(ctx, nsteps);
+    if (rc) return rc;
+    CK(cudaEventRecord(ctx->ev1, ctx->st));
+    ctx->last_steps = nsteps;
+    CK(cudaGetLastError());
+    return RBF_OK;
+}
+
+int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int64_t *kernel_launches) {
+    if (!ctx) return RBF_EINVAL;
+    DeviceGuard dg(ctx->device);
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (total_ms) *total_ms = ms;
+    if (kernel_ms) *kernel_ms = ctx->last_steps ? ms / ctx->last_steps : 0.0;
+    if (kernel_launches) *kernel_launches = ctx->last_steps;
+    return RBF_OK;
+}
+
+int rbf_get_fields(rbf_ctx *ctx, double *uvwp) {
+    if (!ctx || !uvwp) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_get_fields: not initialised");
+    DeviceGuard dg(ctx->device);
+    DevArr<double> out;
+    CK(out.alloc(4 * ctx->n));
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        if (ctx->prec == RBF_FP32) CK(launch_acm_export<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, out.p, ctx->st));
+        else CK(launch_acm_export<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, out.p, ctx->st));
+        ++ctx->launches;
+    } else {
+        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
+        const double vel = ctx->dx / ctx->lbm_dt, ps = ctx->rho * vel * vel;
+        CK(launch_lbm_fields(ctx->n, ctx->perm.p, ctx->mac.p, vel, ps, ctx->scal.p + 3, out.p, ctx->st));
+        ctx->launches += 4;
+    }
+    CK(cudaMemcpyAsync(uvwp, out.p, 4 * ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_set_fields(rbf_ctx *ctx, const double *uvwp) {
+    if (!ctx || !uvwp) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_set_fields: not initialised");
+    if (ctx->solver != RBF_SOLVER_ACM) return fail(ctx, RBF_EINVAL, "rbf_set_fields: ACM only (use rbf_lbm_set_populations)");
+    DeviceGuard dg(ctx->device);
+    DevArr<double> in;
+    CK(in.alloc(4 * ctx->n));
+    CK(cudaMemcpyAsync(in.p, uvwp, 4 * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    const int slot = (ctx->parity + 1) & 1;  // read by the next pressure sweep
+    if (ctx->prec == RBF_FP32) {
+        CK(launch_acm_import<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, in.p, ctx->st));
+        CK(acm_launch_vmax<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), slot, ctx->st));
+    } else {
+        CK(launch_acm_import<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, in.p, ctx->st));
+        CK(acm_launch_vmax<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), slot, ctx->st));
+    }
+    ctx->launches += 2;
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_lbm_get_populations(rbf_ctx *ctx, double *f) {
+    if (!ctx || !f) return RBF_EINVAL;
+    if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_get_populations: no LBM state");
+    DeviceGuard dg(ctx->device);
+    DevArr<double> out;
+    CK(out.alloc((size_t)ctx->q * ctx->n));
+    if (ctx->prec == RBF_FP32) CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
+    else CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(f, out.p, out.n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f) {
+    if (!ctx || !f) return RBF_EINVAL;
+    if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_set_populations: no LBM state");
+    DeviceGuard dg(ctx->device);
+    DevArr<double> in;
+    CK(in.alloc((size_t)ctx->q * ctx->n));
+    CK(cudaMemcpyAsync(in.p, f, in.n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->prec == RBF_FP32) CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    else CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    ++ctx->launches;
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
+namespace {
+int ensure_probes(rbf_ctx *ctx, int m_p) {
+    if (ctx->m_p == m_p && ctx->pidx.p) return RBF_OK;
+    const int64_t tot = 5LL * m_p * m_p;
+    const int n_l = ctx->n_l;
+    DevArr<double> pts;
+    DevArr<int32_t> flag, scan, tmp;
+    CK(pts.alloc(3 * tot)); CK(flag.alloc(tot + 1)); CK(scan.alloc(tot + 1)); CK(tmp.alloc(scan_tmp_len(tot + 1)));
+    CK(flag.zero(ctx->st));
+    k_probe_points<<<nblk(tot), 256, 0, ctx->st>>>(m_p, ctx->c[0], ctx->c[1], ctx->c[2], ctx->r, ctx->has_sphere, pts.p, flag.p);
+    CK(launch_scan_i32(flag.p, scan.p, tot + 1, tmp.p, tmp.n, ctx->st, &ctx->launches));
+    int32_t nfl = 0;
+    CK(cudaMemcpyAsync(&nfl, scan.p + tot, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->np_fluid = nfl;
+    CK(ctx->pxyz.alloc(3 * std::max<int64_t>(nfl, 1)));
+    k_probe_compact<<<nblk(tot), 256, 0, ctx->st>>>(tot, pts.p, flag.p, scan.p, ctx->pxyz.p);
+    ctx->launches += 2;
+    CK(ctx->pidx.alloc(std::max<int64_t>(nfl, 1) * n_l));
+    CK(ctx->pw.alloc(std::max<int64_t>(nfl, 1) * n_l));
+    CK(ctx->status.zero(ctx->st));
+    if (nfl > 0) {
+        CK(launch_knn(nfl, ctx->pxyz.p, nullptr, ctx->xyz.p, ctx->perm.p, ctx->type.p, 0, ctx->G, ctx->cstart.p,
+                      ctx->citems.p, n_l, ctx->pidx.p, n_l, 0, ctx->status.p, ctx->st));
+        OpSpec op{OP_INTERP, {0.0, 0.0, 0.0}};
+        DevArr<OpSpec> d_op;
+        CK(d_op.alloc(1));
+        CK(cudaMemcpyAsync(d_op.p, &op, sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
+        CK(launch_weights(nfl, ctx->xyz.p, ctx->pxyz.p, nullptr, 0, n_l, ctx->pidx.p, ctx->phs_k, ctx->mono_m, 1,
+                          d_op.p, 1, ctx->pw.p, nullptr, ctx->status.p + 1, ctx->st));
+        ctx->launches += 2;
+    }
+    int32_t st2[2] = {0, 0};
+    CK(cudaMemcpyAsync(st2, ctx->status.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (st2[0] || st2[1]) return fail(ctx, RBF_ESINGULAR, "probe stencils failed");
+    ctx->m_p = m_p;
+    return RBF_OK;
+}
+
+// q = mean probe v_x (physical units), FP64
+int probe_q(rbf_ctx *ctx, int m_p, double *qout) {
+    int rc = ensure_probes(ctx, m_p);
+    if (rc) return rc;
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        if (ctx->prec == RBF_FP32) CK(launch_probe_sum<float>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        else CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        ctx->launches += 2;
+    } else {
+        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        ctx->launches += 3;
+    }
+    double s = 0.0;
+    CK(cudaMemcpyAsync(&s, ctx->scal.p + 4, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->solver == RBF_SOLVER_LBM) s *= ctx->dx / ctx->lbm_dt;
+    *qout = s / (5.0 * m_p * m_p);
+    return RBF_OK;
+}
+}  // namespace
+
+int rbf_permeability(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_permeability: not initialised");
+    if (m_p < 1 || m_p > 512) return fail(ctx, RBF_EINVAL, "rbf_permeability: m_p must lie in 1..512");
+    DeviceGuard dg(ctx->device);
+    double qq = 0.0;
+    int rc = probe_q(ctx, m_p, &qq);
+    if (rc) return rc;
+    const double *g = ctx->prm.g;
+    const double gmag = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (q) *q = qq;
+    if (k_over_d2) *k_over_d2 = gmag > 0.0 ? qq * ctx->prm.nu / gmag : 0.0;
+    return RBF_OK;
+}
+
+int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
+    if (!ctx || !F) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_drag: not initialised");
+    if (!ctx->has_sphere) return fail(ctx, RBF_EINVAL, "rbf_drag: set the sphere first");
+    DeviceGuard dg(ctx->device);
+    const double mu = ctx->rho * ctx->prm.nu;
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        if (ctx->prec == RBF_FP32) {
+            FieldView<float> f{ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, 1, 1.0, 0.0, 1.0};
+            CK(launch_drag<float>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
+        } else {
+            FieldView<double> f{ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, 1, 1.0, 0.0, 1.0};
+            CK(launch_drag<double>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
+        }
+        ctx->launches += 2;
+    } else {
+        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
+        double sums[4];
+        CK(cudaMemcpyAsync(sums, ctx->scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        const double vel = ctx->dx / ctx->lbm_dt;
+        FieldView<double> f{ctx->mac.p, ctx->mac.p + 1, ctx->mac.p + 2, ctx->mac.p + 3, 4, vel,
+                            sums[3] / (double)ctx->n, ctx->rho * vel * vel / 3.0};
+        CK(launch_drag<double>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
+        ctx->launches += 5;
+    }
+    double Fs[3];
+    CK(cudaMemcpyAsync(Fs, ctx->scal.p + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const double A = wall_area_of(ctx->r);
+    for (int a = 0; a < 3; ++a) F[a] = ctx->nb ? A / (double)ctx->nb * Fs[a] : 0.0;
+    if (K) {
+        double qq = 0.0;
+        int rc = probe_q(ctx, m_p > 0 ? m_p : 32, &qq);
+        if (rc) return rc;
+        *K = F[0] / (6.0 * M_PI * ctx->r * porosity_of(ctx->r) * qq * mu);
+    }
+    return RBF_OK;
+}
+
+int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
+    if (!ctx || !opts || !res) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_solve: not initialised");
+    if (opts->max_steps < 1 || !(opts->tol > 0.0)) return fail(ctx, RBF_EINVAL, "rbf_solve: bad options");
+    DeviceGuard dg(ctx->device);
+    const int every = opts->check_every > 0 ? opts->check_every : 100;
+    const int m_p = opts->m_p > 0 ? opts->m_p : 32;
+    std::memset(res, 0, sizeof(*res));
+    double kprev = NAN;
+    int64_t done = 0;
+    while (done < opts->max_steps) {
+        int64_t chunk = std::min<int64_t>(every, opts->max_steps - done);
+        double crit = NAN;
+        if (ctx->solver == RBF_SOLVER_ACM) {
+            int rc = run_steps(ctx, chunk - 1);
+            if (rc) return rc;
+            if (ctx->prec == RBF_FP32) for (int a = 0; a < 3; ++a) CK(cudaMemcpyAsync(ctx->a32[7 + a].p, ctx->a32[a].p, ctx->npad * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+            else for (int a = 0; a < 3; ++a) CK(cudaMemcpyAsync(ctx->a64[7 + a].p, ctx->a64[a].p, ctx->npad * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+            rc = run_steps(ctx, 1);
+            if (rc) return rc;
+            if (ctx->prec == RBF_FP32) CK(launch_residual<float>(ctx->n, ctx->type.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[7].p, ctx->a32[8].p, ctx->a32[9].p, ctx->partial.p, ctx->scal.p + 12, ctx->st));
+            else CK(launch_residual<double>(ctx->n, ctx->type.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[7].p, ctx->a64[8].p, ctx->a64[9].p, ctx->partial.p, ctx->scal.p + 12, ctx->st));
+            ctx->launches += 2;
+            double r2[2];
+            CK(cudaMemcpyAsync(r2, ctx->scal.p + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            done += chunk;
+            if (!std::isfinite(r2[0]) || !std::isfinite(r2[1])) {
+                res->steps = done;
+                return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite velocity");
+            }
+            crit = r2[1] > 0.0 ? std::sqrt(r2[0]) / std::sqrt(r2[1]) : 0.0;
+            res->residual = crit;
+            if (crit < opts->tol && r2[1] > 0.0) { res->converged = 1; break; }
+        } else {
+            int rc = run_steps(ctx, chunk);
+            if (rc) return rc;
+            done += chunk;
+            double k = 0.0;
+            rc = rbf_permeability(ctx, m_p, &k, nullptr);
+            if (rc) return rc;
+            if (!std::isfinite(k)) {
+                res->steps = done;
+                return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite permeability");
+            }
+            if (std::isfinite(kprev) && k != 0.0) {
+                crit = std::fabs(k - kprev) / std::fabs(k);
+                res->residual = crit;
+                if (crit < opts->tol) { kprev = k; res->converged = 1; break; }
+            }
+            kprev = k;
+        }
+    }
+    res->steps = done;
+    double k = 0.0;
+    int rc = rbf_permeability(ctx, m_p, &k, nullptr);
+    if (rc) return rc;
+    res->k_over_d2 = k;
+    return res->converged ? RBF_OK : fail(ctx, RBF_ENOTCONVERGED, "rbf_solve: step cap reached");
+}
+
+}  // extern "C"

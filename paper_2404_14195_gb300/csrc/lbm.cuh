@@ -1,0 +1,35 @@
+// lbm.cuh — argument block and launchers of the meshless LBM kernels.
+#pragma once
+#include "internal.cuh"
+
+namespace rbf {
+
+template <typename T>
+struct LbmArgs {
+    int64_t n, npad;
+    int n_l;
+    const int32_t *idx;    // SELL [slice][j][lane]
+    const T *w;            // SELL [slice][k-1][j][lane], k = 1..q-1
+    const uint32_t *mask;  // unknown populations of wall nodes (bit k)
+    const T *fin;          // f~_post, [q][npad]
+    T *fout;
+    T tp_inv, tm_inv;      // 1/tau+, 1/tau-
+    T gx, gy, gz;          // g_lb
+};
+
+const int *host_velocity_set(int q);
+double host_lattice_weight(int q, int k);
+
+template <typename T>
+cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st);
+template <typename T>
+cudaError_t lbm_launch_init(const LbmArgs<T> &a, int q, cudaStream_t st);
+cudaError_t lbm_launch_masks(int64_t n, int q, const uint8_t *type, const double *nrm, uint32_t *mask, cudaStream_t st);
+template <typename T>
+cudaError_t lbm_launch_export(int64_t n, int64_t npad, int q, const T *f, const int32_t *perm, double *out, cudaStream_t st);
+template <typename T>
+cudaError_t lbm_launch_import(int64_t n, int64_t npad, int q, T *f, const int32_t *perm, const double *in, cudaStream_t st);
+template <typename T>
+cudaError_t lbm_launch_macro(int64_t n, int64_t npad, int q, const T *f, const double g[3], double *out, cudaStream_t st);
+
+}  // namespace rbf

@@ -1,0 +1,291 @@
+// reduce.cu — FP64 reductions and field marshalling.
+//
+//  * residual: |v - v_prev|_2 / |v|_2 over fluid nodes;
+//  * permeability (Eq. k_definition): probe interpolation of v_x and its mean;
+//  * drag (Eqs. stress_tensor_force, integration_force): sigma . n summed over
+//    wall nodes with the wall nodes' gradient weights;
+//  * min / sum helpers.
+// Every reduction writes one FP64 partial per block and a single block adds the
+// partials in a fixed order, so results are reproducible run to run.
+#include "reduce.cuh"
+
+namespace rbf {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// block sum of ncomp values per thread into partial[blockIdx.x * ncomp + c]
+template <int NC>
+__device__ __forceinline__ void block_partial(double (&v)[NC], double *partial) {
+    __shared__ double red[8][NC];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = warp_sum(v[c]);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) red[w][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x < NC) {
+        double s = 0.0;
+        for (int t = 0; t < (int)(blockDim.x >> 5); ++t) s += red[t][threadIdx.x];
+        partial[blockIdx.x * NC + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_final_sum(const double *partial, int64_t nb, int nc, double *out) {
+    // one warp per component, strided over blocks, fixed order
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c >= nc) return;
+    double s = 0.0;
+    for (int64_t b = lane; b < nb; b += 32) s += partial[b * nc + c];
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+}
+
+static cudaError_t final_sum(const double *partial, int64_t nb, int nc, double *out, cudaStream_t st) {
+    k_final_sum<<<1, 32 * nc, 0, st>>>(partial, nb, nc, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(int64_t n, const uint8_t *type, const T *u, const T *v, const T *w,
+                                                  const T *uo, const T *vo, const T *wo, double *partial) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double acc[2] = {0.0, 0.0};
+    if (i < n && !type[i]) {
+        double a = (double)u[i] - (double)uo[i], b = (double)v[i] - (double)vo[i], c = (double)w[i] - (double)wo[i];
+        acc[0] = a * a + b * b + c * c;
+        acc[1] = (double)u[i] * u[i] + (double)v[i] * v[i] + (double)w[i] * w[i];
+    }
+    block_partial<2>(acc, partial);
+}
+
+template <typename T>
+cudaError_t launch_residual(int64_t n, const uint8_t *type, const T *u, const T *v, const T *w, const T *uo,
+                            const T *vo, const T *wo, double *partial, double *out2, cudaStream_t st) {
+    int64_t nb = (n + 255) / 256;
+    k_residual<T><<<(unsigned)nb, 256, 0, st>>>(n, type, u, v, w, uo, vo, wo, partial);
+    return final_sum(partial, nb, 2, out2, st);
+}
+
+// probe interpolation: out_sum = sum_p sum_j w_pj vx[S_p(j)] * scale
+template <typename T>
+__global__ void __launch_bounds__(256) k_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w,
+                                                   const T *vx, int64_t stride, double *partial) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double acc[1] = {0.0};
+    if (p < np) {
+        double s = 0.0;
+        for (int j = 0; j < n_l; ++j) s += w[p * n_l + j] * (double)vx[idx[p * n_l + j] * stride];
+        acc[0] = s;
+    }
+    block_partial<1>(acc, partial);
+}
+
+template <typename T>
+cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, int64_t stride,
+                             double *partial, double *out, cudaStream_t st) {
+    if (np == 0) return cudaMemsetAsync(out, 0, sizeof(double), st);
+    int64_t nb = (np + 255) / 256;
+    k_probe_sum<T><<<(unsigned)nb, 256, 0, st>>>(np, n_l, idx, w, vx, stride, partial);
+    return final_sum(partial, nb, 1, out, st);
+}
+
+// sigma . n at wall nodes: sigma_ij = -p d_ij + rho nu (d_j v_i + d_i v_j).
+// Velocity components and pressure are read through (pointer, stride) views and
+// scaled to physical units: v = vs * vel, p = (praw - p0) * ps.
+template <typename T>
+__global__ void __launch_bounds__(256) k_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx,
+                                              const double *wg, const double *nrm, FieldView<T> f, double mu,
+                                              double *partial) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (b < nb) {
+        int64_t i = wall[b];
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // G[comp][dir] = d v_comp / d x_dir
+        const double *gx = wg + b * 3 * n_l, *gy = gx + n_l, *gz = gy + n_l;
+        for (int j = 0; j < n_l; ++j) {
+            int64_t q = idx[i * n_l + j];
+            double vq[3] = {(double)f.u[q * f.stride] * f.vel, (double)f.v[q * f.stride] * f.vel,
+                            (double)f.w[q * f.stride] * f.vel};
+            for (int c = 0; c < 3; ++c) {
+                G[c][0] += gx[j] * vq[c];
+                G[c][1] += gy[j] * vq[c];
+                G[c][2] += gz[j] * vq[c];
+            }
+        }
+        double p = ((double)f.p[i * f.stride] - f.p0) * f.ps;
+        double n3[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+        for (int a = 0; a < 3; ++a) {
+            double s = -p * n3[a];
+            for (int c = 0; c < 3; ++c) s += mu * (G[a][c] + G[c][a]) * n3[c];
+            acc[a] = s;
+        }
+    }
+    block_partial<3>(acc, partial);
+}
+
+template <typename T>
+cudaError_t launch_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx, const double *wg,
+                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out3,
+                        cudaStream_t st) {
+    if (nb == 0) return cudaMemsetAsync(out3, 0, 3 * sizeof(double), st);
+    int64_t nbl = (nb + 255) / 256;
+    k_drag<T><<<(unsigned)nbl, 256, 0, st>>>(nb, n_l, wall, idx, wg, nrm, f, mu, partial);
+    return final_sum(partial, nbl, 3, out3, st);
+}
+
+__global__ void k_min(const double *in, int64_t n, double *partial) {
+    __shared__ double red[8];
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v = i < n ? in[i] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = red[0];
+        for (int t = 1; t < (int)(blockDim.x >> 5); ++t) m = fmin(m, red[t]);
+        partial[blockIdx.x] = m;
+    }
+}
+__global__ void k_min_final(const double *partial, int64_t nb, double *out) {
+    double v = __longlong_as_double(0x7ff0000000000000LL);
+    for (int64_t b = threadIdx.x; b < nb; b += 32) v = fmin(v, partial[b]);
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) *out = v;
+}
+cudaError_t launch_min_f64(const double *in, int64_t n, double *partial, double *out, cudaStream_t st) {
+    int64_t nb = (n + 255) / 256;
+    k_min<<<(unsigned)nb, 256, 0, st>>>(in, n, partial);
+    k_min_final<<<1, 32, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+// sum of in[i * stride + c] for c < ncomp (ncomp <= 4)
+__global__ void k_sum_strided(const double *in, int64_t n, int stride, int ncomp, double *partial) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    if (i < n)
+        for (int c = 0; c < ncomp; ++c) acc[c] = in[i * stride + c];
+    block_partial<4>(acc, partial);
+}
+cudaError_t launch_sum_f64(const double *in, int64_t n, int stride, int ncomp, double *partial, double *out,
+                           cudaStream_t st) {
+    int64_t nb = (n + 255) / 256;
+    k_sum_strided<<<(unsigned)nb, 256, 0, st>>>(in, n, stride, ncomp, partial);
+    return final_sum(partial, nb, 4, out, st);
+}
+
+// ---- ACM fields <-> caller order, FP64 ---------------------------------------
+template <typename T>
+__global__ void k_acm_export(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *p,
+                             double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = perm[i];
+    out[4 * o] = (double)u[i]; out[4 * o + 1] = (double)v[i]; out[4 * o + 2] = (double)w[i]; out[4 * o + 3] = (double)p[i];
+}
+template <typename T>
+__global__ void k_acm_import(int64_t n, const int32_t *perm, T *u, T *v, T *w, T *p, const double *in) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = perm[i];
+    u[i] = (T)in[4 * o]; v[i] = (T)in[4 * o + 1]; w[i] = (T)in[4 * o + 2]; p[i] = (T)in[4 * o + 3];
+}
+template <typename T>
+cudaError_t launch_acm_export(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *p,
+                              double *out, cudaStream_t st) {
+    k_acm_export<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, u, v, w, p, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_acm_import(int64_t n, const int32_t *perm, T *u, T *v, T *w, T *p, const double *in,
+                              cudaStream_t st) {
+    k_acm_import<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, u, v, w, p, in);
+    return cudaGetLastError();
+}
+
+// LBM macro buffer (sorted, lattice units, (vx, vy, vz, drho)) -> physical uvwp, caller order
+__global__ void k_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
+                             const double *drho_sum, double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = perm[i];
+    double mean = drho_sum[0] / (double)n;
+    out[4 * o] = mac[4 * i] * vel;
+    out[4 * o + 1] = mac[4 * i + 1] * vel;
+    out[4 * o + 2] = mac[4 * i + 2] * vel;
+    out[4 * o + 3] = (mac[4 * i + 3] - mean) * (1.0 / 3.0) * ps;
+}
+cudaError_t launch_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
+                              const double *drho_sum, double *out, cudaStream_t st) {
+    k_lbm_fields<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, mac, vel, ps, drho_sum, out);
+    return cudaGetLastError();
+}
+
+// non-finite detector: sets *flag when any value is NaN/Inf
+template <typename T>
+__global__ void k_nonfinite(const T *a, int64_t n, int32_t *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && !isfinite((double)a[i])) atomicExch(flag, 1);
+}
+template <typename T>
+cudaError_t launch_nonfinite(const T *a, int64_t n, int32_t *flag, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_nonfinite<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
+// caller-order gathers for rbf_get_stencils / rbf_get_weights
+__global__ void k_export_stencils(int64_t n, int n_l, const int32_t *perm, const int32_t *iperm,
+                                  const int32_t *idx, int32_t *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * n_l) return;
+    int64_t o = t / n_l;
+    int j = (int)(t - o * n_l);
+    out[t] = perm[idx[(int64_t)iperm[o] * n_l + j]];
+}
+cudaError_t launch_export_stencils(int64_t n, int n_l, const int32_t *perm, const int32_t *iperm,
+                                   const int32_t *idx, int32_t *out, cudaStream_t st) {
+    int64_t tot = n * n_l;
+    k_export_stencils<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n_l, perm, iperm, idx, out);
+    return cudaGetLastError();
+}
+// rows of w (sorted row r = node, n_ops operators) for operator op -> out[caller][j];
+// rowmap (optional): caller node -> row (-1: no row, output NaN)
+__global__ void k_export_weights(int64_t n, int n_l, int n_ops, int op, const int32_t *iperm, const int32_t *rowmap,
+                                 const double *w, double *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * n_l) return;
+    int64_t o = t / n_l;
+    int j = (int)(t - o * n_l);
+    int64_t r = iperm[o];
+    if (rowmap) r = rowmap[r];
+    out[t] = r < 0 ? __longlong_as_double(0x7ff8000000000000LL) : w[(r * n_ops + op) * n_l + j];
+}
+cudaError_t launch_export_weights(int64_t n, int n_l, int n_ops, int op, const int32_t *iperm, const int32_t *rowmap,
+                                  const double *w, double *out, cudaStream_t st) {
+    int64_t tot = n * n_l;
+    k_export_weights<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, n_l, n_ops, op, iperm, rowmap, w, out);
+    return cudaGetLastError();
+}
+
+#define RBF_RED_INST(T)                                                                                         \
+    template cudaError_t launch_residual<T>(int64_t, const uint8_t *, const T *, const T *, const T *, const T *, \
+                                            const T *, const T *, double *, double *, cudaStream_t);            \
+    template cudaError_t launch_probe_sum<T>(int64_t, int, const int32_t *, const double *, const T *, int64_t,  \
+                                             double *, double *, cudaStream_t);                                 \
+    template cudaError_t launch_drag<T>(int64_t, int, const int32_t *, const int32_t *, const double *,          \
+                                        const double *, const FieldView<T> &, double, double *, double *,       \
+                                        cudaStream_t);                                                          \
+    template cudaError_t launch_acm_export<T>(int64_t, const int32_t *, const T *, const T *, const T *,         \
+                                              const T *, double *, cudaStream_t);                               \
+    template cudaError_t launch_acm_import<T>(int64_t, const int32_t *, T *, T *, T *, T *, const double *,      \
+                                              cudaStream_t);                                                    \
+    template cudaError_t launch_nonfinite<T>(const T *, int64_t, int32_t *, cudaStream_t);
+RBF_RED_INST(float)
+RBF_RED_INST(double)
+
+}  // namespace rbf

@@ -1,0 +1,42 @@
+// reduce.cuh — launchers of the FP64 reductions and field marshalling kernels.
+#pragma once
+#include "internal.cuh"
+
+namespace rbf {
+
+// Read-only view of a velocity / pressure field: component pointers with a
+// common element stride, scaled to physical units v = raw * vel,
+// p = (raw - p0) * ps.
+template <typename T>
+struct FieldView {
+    const T *u, *v, *w, *p;
+    int64_t stride;
+    double vel, p0, ps;
+};
+
+template <typename T>
+cudaError_t launch_residual(int64_t n, const uint8_t *type, const T *u, const T *v, const T *w, const T *uo,
+                            const T *vo, const T *wo, double *partial, double *out2, cudaStream_t st);
+template <typename T>
+cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, int64_t stride,
+                             double *partial, double *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx, const double *wg,
+                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out3,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_acm_export(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *p,
+                              double *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_acm_import(int64_t n, const int32_t *perm, T *u, T *v, T *w, T *p, const double *in,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_nonfinite(const T *a, int64_t n, int32_t *flag, cudaStream_t st);
+cudaError_t launch_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
+                              const double *drho_sum, double *out, cudaStream_t st);
+cudaError_t launch_export_stencils(int64_t n, int n_l, const int32_t *perm, const int32_t *iperm,
+                                   const int32_t *idx, int32_t *out, cudaStream_t st);
+cudaError_t launch_export_weights(int64_t n, int n_l, int n_ops, int op, const int32_t *iperm, const int32_t *rowmap,
+                                  const double *w, double *out, cudaStream_t st);
+
+}  // namespace rbf
