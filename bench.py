@@ -1,0 +1,297 @@
+"""Benchmark: meshless D3Q19 TRT LBM steps on GB300, node-steps/s.
+
+Workload (one step = one MLBM time step of the whole cell, stream + bounce-back
++ TRT collision fused in one kernel): the periodic simple-cubic sphere cell of
+radius 0.40 with an h-refined advancing-front fill h(d) = 0.008 + 0.032
+min(1, d / 0.2) (about 150k nodes, 31k on the wall), N_L = 30 nearest
+neighbours, PHS r^3 + quadratic monomials, TRT Lambda = 3/16, tau+ = 0.8,
+nu = 1, g = (1, 0, 0), dx = h_min / 2 = 0.004, FP32 shifted populations.
+Inputs are synthetic (seeded node cloud); the weights (324 MB) exceed the
+129 MB L2, so every step streams them from HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same
+workload (the paper's own code is a single-threaded CPU program that is not
+available here).  Under torchrun (N > 1) every rank runs an independent replica
+of the cell on its own GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-steps/s; time-to-steady-permeability (1e-4 rel) vs plain FP64 on same GPU"
+UNIT = "node-steps/s"
+R, H_MIN, H_MAX, RAMP, SEED = 0.40, 0.008, 0.04, 0.2, 2
+N_L, Q, DX, TAU_P, MAGIC = 30, 19, 0.004, 0.8, 3.0 / 16.0
+
+
+def workload():
+    import synth
+    return synth.refined_cell(r=R, h_min=H_MIN, h_max=H_MAX, ramp=RAMP, seed=SEED)
+
+
+def bytes_per_node_step(q=Q, n_l=N_L, elt=4):
+    """Algorithmic bytes of one fused LBM step per node: the q-1 interpolation
+    weight rows and the stencil indices streamed once, every population read
+    once and written once (FP32)."""
+    return elt * (q - 1) * n_l + 4 * n_l + 2 * elt * q
+
+
+def config_dict(n, nb):
+    return {
+        "workload": (f"MLBM D3Q19 TRT FP32 step, periodic SC sphere cell r={R}, h-refined fill "
+                     f"h(d)={H_MIN}+{H_MAX - H_MIN:.3f}*min(1,d/{RAMP}), N={n} nodes ({nb} wall), "
+                     f"N_L={N_L}, PHS r^3 + m=2, dx={DX}"),
+        "nodes": n, "wall_nodes": nb, "n_l": N_L, "q": Q, "precision": "fp32 fields+weights, fp64 weight solve",
+        "l2": "inputs larger than L2 (324 MB FP32 weights streamed per step)",
+        "seed": SEED,
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the fused LBM kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "lbm_step_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2404_14195_gb300", "csrc", "lbm.cu"), "rb").read()
+        if rec.get("lbm_cu_sha256") == hashlib.sha256(src).hexdigest() and rec.get("nodes_full"):
+            return rec["dram_bytes_per_launch_full"]
+    except Exception:
+        pass
+    return None
+
+
+def oracle_baseline(case, budget_s=12.0, max_steps=200):
+    """The CPU oracle (FP64, all host cores via OpenMP) on the same cell: stencils
+    and weights untimed, then a bounded number of timed steps."""
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    idx = oracle.knn(case["xyz"], case["xyz"], N_L, grid=True)
+    wk = oracle.lbm_weights(case["xyz"], idx, Q, DX)
+    u = oracle.lbm_units(1.0, TAU_P, DX, (1.0, 0.0, 0.0))
+    tm = oracle.tau_minus(TAU_P, MAGIC)
+    f = oracle.lbm_equilibrium(Q, np.ones(case.n), np.zeros((case.n, 3)))
+    t0 = time.perf_counter()
+    f = oracle.lbm_run(f, Q, case, idx, wk, TAU_P, tm, u["g_lb"], 1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.lbm_run(f, Q, case, idx, wk, TAU_P, tm, u["g_lb"], steps)
+    dt = time.perf_counter() - t0
+    return {"value": case.n * steps / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle MLBM steps of the full {case.n}-node cell (stencils and weights untimed)",
+            "seconds": dt, "steps": steps}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = workload()
+    base = oracle_baseline(case, budget_s=60.0, max_steps=max(args.steps, 3))
+    line = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": base["steps"],
+            "warmup": 0, "ms_per_step": 1e3 * base["seconds"] / base["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config_dict(case.n, int((case["type"] == 1).sum())),
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "FP64 CPU oracle of the paper's method (the paper's own CPU code is not available)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--variant", type=int, default=1, help="LBM kernel: 0 node per thread, 1 pair per warp")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    import paper_2404_14195_gb300 as rbf
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    rbf._build.build()
+    case = workload()
+    n, nb = case.n, int((case["type"] == 1).sum())
+
+    s = rbf.Solver(local)
+    s.set_case(case)
+    s.build_stencils(N_L)
+    s.compute_weights(k=3, m=2, solver=rbf.RBF_SOLVER_LBM, q=Q, dx=DX)
+    s.init(precision=rbf.RBF_FP32, nu=1.0, g=(1.0, 0.0, 0.0), tau_plus=TAU_P, magic=MAGIC)
+    s.set_kernel_variant(args.variant)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    l0 = s.launch_count()
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(args.steps)
+        total_ms, per_launch_ms, nlaunch = s.last_step_timing()  # waits for the events
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+    launches = s.launch_count() - l0
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax_ms = float(t.item())
+    value = ws * n * args.steps / (tmax_ms / 1e3)
+
+    # per-launch kernel time with event pairs (eager launches, after the timed region)
+    prof_ms = float(s.profile_steps(200)[0])
+    k, _ = s.permeability(32)
+
+    # end to end through the public API with pinned host buffers: every step uploads
+    # its input populations and reads back the step's fields
+    f_host = torch.empty((Q, n), dtype=torch.float64, pin_memory=True).numpy()
+    f_host[:] = s.lbm_get_populations()
+    out_host = torch.empty((n, 4), dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(3):
+        s.lbm_set_populations(f_host); s.step(1); out_host[:] = s.get_fields()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.lbm_set_populations(f_host)
+        s.step(1)
+        out_host[:] = s.get_fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = ws * n * args.e2e_steps / float(e2e_t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    bpl = bytes_per_node_step() * n
+    achieved = bpl / (per_launch_ms / 1e3) / 1e9
+    cpu = None if (args.no_cpu_baseline or ws > 1) else oracle_baseline(case)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded node cloud; the paper's datasets are not used)",
+        "config": config_dict(n, nb) | {"parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": kernel_traffic(),
+                     "kernel": ["k_lbm_step<float,19>", "k_lbm_step_pairs<float,19,5>"][args.variant],
+                     "bytes_per_launch": bpl,
+                     "per_launch_ms_timed_region": per_launch_ms, "per_launch_ms_event_pairs": prof_ms,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback"},
+        "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(Q * n * 8),
+                "d2h_bytes_per_step": int(4 * n * 8), "steps": args.e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "k_over_d2_after_run": k,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

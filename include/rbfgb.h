@@ -184,6 +184,19 @@ int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res);
  * that call (the fused LBM kernel; the ACM predictor).  */
 int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int64_t *kernel_launches);
 
+/* Advance nsteps steps with eager launches, timing every kernel launch with a
+ * CUDA event pair on the context stream.  kernel_ms[c] receives the mean
+ * duration (ms) of one launch of kernel class c; *n_classes the number of
+ * classes: LBM 1 (the fused step); ACM 4 (predictor, pressure, wall pressure,
+ * correction).  kernel_ms must hold 4 doubles.  1 <= nsteps <= 4096. */
+int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classes);
+
+/* Kernel variant of the fused LBM step: 0 one node per thread (all q
+ * populations of a node in one thread); 1 one opposite-population pair per warp
+ * (q-1)/2 warps per 32-node slice, moments reduced in shared memory (default).
+ * Both compute the same step; the choice only changes the schedule. */
+int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
+
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
 

@@ -53,6 +53,7 @@ def _load():
             P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
             sig = {
                 "orc_knn": [I64, P, I64, P, I, P],
+                "orc_knn_grid": [I64, P, I64, P, I, P],
                 "orc_monomials": [I, P],
                 "orc_rbf_weights": [I64, P, I64, P, I, I, P, I, I, I, P, P, I, P],
                 "orc_acm_run": [I64, P, P, I, P, P, I64, P, P, P, P, I, I, P, P, P, P, P],
@@ -122,13 +123,15 @@ def wall_area(r: float) -> float:
 # ---------------------------------------------------------------------------
 # stencils and weights: meshless discretisation and approximation section
 # ---------------------------------------------------------------------------
-def knn(xyz, queries, n_l: int) -> np.ndarray:
+def knn(xyz, queries, n_l: int, grid=None) -> np.ndarray:
     """S = the n_l nearest nodes of each query by periodic distance, ordered by
-    (squared distance, node index); brute force.  Queries that are nodes get
-    themselves first (S_i(1) = i)."""
+    (squared distance, node index).  Queries that are nodes get themselves first
+    (S_i(1) = i).  Brute force for small problems; a cell-grid search with the
+    same result (grid=True) for large ones."""
     xyz, q = _f64(xyz), _f64(queries)
     out = np.empty((len(q), n_l), np.int32)
-    rc = _load().orc_knn(len(xyz), _p(xyz), len(q), _p(q), n_l, _p(out))
+    fn = _load().orc_knn if (grid is None and len(xyz) * len(q) <= 4e8) or grid is False else _load().orc_knn_grid
+    rc = fn(len(xyz), _p(xyz), len(q), _p(q), n_l, _p(out))
     if rc != 0:
         raise ValueError(f"knn failed ({rc})")
     return out

@@ -65,6 +65,68 @@ int orc_knn(int64_t n, const double *xyz, int64_t nq, const double *q, int n_l, 
     return bad ? -2 : 0;
 }
 
+/* Same neighbour lists as orc_knn, found through a uniform periodic cell grid:
+ * every node within distance R of the query is examined (all cells overlapping
+ * the ball), and R is doubled until the n_l-th best distance is below R, so no
+ * unexamined node can be closer or tie.  Used for large clouds. */
+int orc_knn_grid(int64_t n, const double *xyz, int64_t nq, const double *q, int n_l, int32_t *out) {
+    if (n_l < 1 || n_l > n || n_l > ORC_MAXN) return -1;
+    int G = (int)cbrt((double)n / 8.0);
+    if (G < 1) G = 1;
+    if (G > 256) G = 256;
+    const double cs = 1.0 / G;
+    int64_t ncell = (int64_t)G * G * G;
+    int64_t *head = malloc(sizeof(int64_t) * ncell), *next = malloc(sizeof(int64_t) * n);
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t j = n - 1; j >= 0; --j) {
+        int a = (int)(xyz[3 * j] * G), b = (int)(xyz[3 * j + 1] * G), c = (int)(xyz[3 * j + 2] * G);
+        a = a < 0 ? 0 : (a >= G ? G - 1 : a); b = b < 0 ? 0 : (b >= G ? G - 1 : b); c = c < 0 ? 0 : (c >= G ? G - 1 : c);
+        int64_t cell = ((int64_t)a * G + b) * G + c;
+        next[j] = head[cell];
+        head[cell] = j;
+    }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < nq; ++t) {
+        double bd[ORC_MAXN];
+        int64_t bi[ORC_MAXN];
+        double qx = q[3 * t] - floor(q[3 * t]), qy = q[3 * t + 1] - floor(q[3 * t + 1]), qz = q[3 * t + 2] - floor(q[3 * t + 2]);
+        int ca = (int)(qx * G), cb = (int)(qy * G), cc = (int)(qz * G);
+        ca = ca >= G ? G - 1 : ca; cb = cb >= G ? G - 1 : cb; cc = cc >= G ? G - 1 : cc;
+        for (double R = 1.5 * cs;; R *= 2.0) {
+            int reach = (int)ceil(R / cs);
+            int full = 2 * reach + 1 >= G;
+            int lo = full ? 0 : -reach, hi = full ? G - 1 : reach;
+            int cnt = 0;
+            for (int da = lo; da <= hi; ++da)
+                for (int db = lo; db <= hi; ++db)
+                    for (int dc = lo; dc <= hi; ++dc) {
+                        int a = full ? da : ((ca + da) % G + G) % G;
+                        int b = full ? db : ((cb + db) % G + G) % G;
+                        int c = full ? dc : ((cc + dc) % G + G) % G;
+                        for (int64_t j = head[((int64_t)a * G + b) * G + c]; j >= 0; j = next[j]) {
+                            double dx = orc_mimg(xyz[3 * j] - qx), dy = orc_mimg(xyz[3 * j + 1] - qy);
+                            double dz = orc_mimg(xyz[3 * j + 2] - qz);
+                            double d2 = dx * dx + dy * dy + dz * dz;
+                            if (cnt == n_l && (d2 > bd[cnt - 1] || (d2 == bd[cnt - 1] && j > bi[cnt - 1]))) continue;
+                            int pos = (cnt < n_l) ? cnt++ : cnt - 1;
+                            while (pos > 0 && (bd[pos - 1] > d2 || (bd[pos - 1] == d2 && bi[pos - 1] > j))) {
+                                bd[pos] = bd[pos - 1]; bi[pos] = bi[pos - 1]; --pos;
+                            }
+                            bd[pos] = d2; bi[pos] = j;
+                        }
+                    }
+            if ((cnt == n_l && bd[n_l - 1] < R * R) || full) {
+                if (cnt < n_l) bad = 1;
+                for (int k = 0; k < n_l; ++k) out[t * n_l + k] = (int32_t)(k < cnt ? bi[k] : 0);
+                break;
+            }
+        }
+    }
+    free(head); free(next);
+    return bad ? -2 : 0;
+}
+
 /* ---- RBF-FD weights (Eqs. operatorApprox, rbfScaling, augmentedSystem) -------
  * Basis: polyharmonic spline Phi(r) = r^k (odd k) in the scaled distance
  * r / delta_i, augmented with the N_p = C(m+3, 3) monomials of total degree <= m

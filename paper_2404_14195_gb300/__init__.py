@@ -86,6 +86,8 @@ ABI = {
     "rbf_solve": (_I, [_P, ctypes.POINTER(rbf_solve_opts), ctypes.POINTER(rbf_solve_result)]),
     "rbf_last_step_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "rbf_launch_count": (_I64, [_P]),
+    "rbf_profile_steps": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
+    "rbf_set_kernel_variant": (_I, [_P, _I]),
 }
 
 
@@ -250,6 +252,19 @@ class Solver:
         t, k, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
         self._ck(self._L.rbf_last_step_timing(self._h, ctypes.byref(t), ctypes.byref(k), ctypes.byref(n)))
         return t.value, k.value, n.value
+
+    def profile_steps(self, nsteps: int):
+        """Mean device time (ms) of one launch of each kernel class over nsteps
+        eagerly launched steps (LBM: [fused step]; ACM: [predict, pressure,
+        wall pressure, correct])."""
+        ms = np.zeros(4)
+        nc = ctypes.c_int()
+        self._ck(self._L.rbf_profile_steps(self._h, int(nsteps), _ptr(ms), ctypes.byref(nc)))
+        return ms[:nc.value].copy()
+
+    def set_kernel_variant(self, variant: int):
+        """0: one node per thread; 1: one population pair per warp (default)."""
+        self._ck(self._L.rbf_set_kernel_variant(self._h, int(variant)))
 
     def launch_count(self) -> int:
         return int(self._L.rbf_launch_count(self._h))

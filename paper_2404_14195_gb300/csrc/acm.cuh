@@ -22,7 +22,8 @@ struct AcmArgs {
 };
 
 template <typename T>
-cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches);
+cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
+                            LaunchRecorder *rec = nullptr);
 template <typename T>
 cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st);
 template <typename T>

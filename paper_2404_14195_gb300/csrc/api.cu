@@ -87,11 +87,12 @@ struct rbf_ctx {
     DevArr<double> pxyz, pw;
     DevArr<int32_t> pidx;
     // scratch
-    DevArr<double> partial, scal, mac, hostbuf_dev;
+    DevArr<double> partial, scal, mac, stage;  // stage: host <-> device field transfers
     DevArr<int32_t> status;
     // graph of `gsteps` steps
     cudaGraphExec_t gexec = nullptr;
-    int gsteps = 0, gparity = -1, gcur = -1, gprec = -1;
+    int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1;
+    int variant = LBM_PAIR_PER_WARP;  // kernel variant of the step
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
     int64_t last_steps = 0;
@@ -227,16 +228,19 @@ LbmArgs<T> lbm_args(rbf_ctx *ctx, DevArr<T> *f, const DevArr<T> &ws, int cur) {
 }
 
 // enqueue `steps` steps starting from (parity, cur); updates them
-cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_t *launches) {
+cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_t *launches,
+                          LaunchRecorder *rec = nullptr) {
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
         if (ctx->solver == RBF_SOLVER_ACM) {
-            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches);
-            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches);
+            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec);
+            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec);
             parity = (parity + ctx->n_p) & 1;
         } else {
-            if (ctx->prec == RBF_FP32) e = lbm_launch_step<float>(lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur), ctx->q, ctx->st);
-            else e = lbm_launch_step<double>(lbm_args<double>(ctx, ctx->f64, ctx->ws64, cur), ctx->q, ctx->st);
+            if (rec) rec->begin(ctx->st, 0);
+            if (ctx->prec == RBF_FP32) e = lbm_launch_step<float>(lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur), ctx->q, ctx->st, ctx->variant);
+            else e = lbm_launch_step<double>(lbm_args<double>(ctx, ctx->f64, ctx->ws64, cur), ctx->q, ctx->st, ctx->variant);
+            if (rec) rec->end(ctx->st);
             ++*launches;
             cur ^= 1;
         }
@@ -250,7 +254,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
     int64_t kl = 0;
     if (full > 0) {
         if (!ctx->gexec || ctx->gparity != ctx->parity || ctx->gcur != ctx->cur || ctx->gprec != ctx->prec ||
-            ctx->gsteps != chunk) {
+            ctx->gsteps != chunk || ctx->gvariant != ctx->variant) {
             drop_graph(ctx);
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -267,6 +271,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
             ctx->gparity = ctx->parity;
             ctx->gcur = ctx->cur;
             ctx->gprec = ctx->prec;
+            ctx->gvariant = ctx->variant;
             ctx->last_kernel_launches = dummy;
         }
         int64_t per_graph = ctx->last_kernel_launches;
@@ -538,8 +543,13 @@ int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, 
     const int n_out = n_ops;
     CK(ctx->ws32.alloc(ctx->npad * n_out * n_l));
     CK(ctx->ws64.alloc(ctx->npad * n_out * n_l));
-    CK(launch_pack_f32(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
-    CK(launch_pack_f64(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+    if (solver == RBF_SOLVER_ACM) {
+        CK(launch_pack_f32(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
+        CK(launch_pack_f64(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+    } else {
+        CK(lbm_launch_pack_f32(n, q, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
+        CK(lbm_launch_pack_f64(n, q, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+    }
     ctx->launches += 2;
     const int64_t nbpad = (nb + 31) & ~31LL;
     if (solver == RBF_SOLVER_ACM) {
@@ -648,6 +658,7 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
         ++ctx->launches;
     }
     CK(ctx->mac.alloc(4 * n));
+    CK(ctx->stage.alloc((size_t)std::max(4, ctx->q) * n));
     {
         const size_t need = (size_t)(4 * (std::max<int64_t>(n, 5LL * 512 * 512) / 256 + 8));
         if (ctx->partial.n < need) CK(ctx->partial.alloc(need));
@@ -683,12 +694,55 @@ int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int6
     return RBF_OK;
 }
 
+int rbf_set_kernel_variant(rbf_ctx *ctx, int variant) {
+    if (!ctx) return RBF_EINVAL;
+    if (variant != LBM_NODE_PER_THREAD && variant != LBM_PAIR_PER_WARP)
+        return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: 0 or 1");
+    ctx->variant = variant;
+    return RBF_OK;
+}
+
+int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classes) {
+    if (!ctx || !kernel_ms) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_profile_steps: not initialised");
+    if (nsteps < 1 || nsteps > 4096) return fail(ctx, RBF_EINVAL, "rbf_profile_steps: 1 <= nsteps <= 4096");
+    DeviceGuard dg(ctx->device);
+    const int per_step = ctx->solver == RBF_SOLVER_ACM ? 1 + 3 * ctx->n_p : 1;
+    const int cap = nsteps * per_step;
+    std::vector<cudaEvent_t> ev(2 * cap, nullptr);
+    std::vector<int> cls(cap, 0);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    LaunchRecorder rec;
+    rec.ev = ev.data();
+    rec.cls = cls.data();
+    rec.cap = cap;
+    int64_t kl = 0;
+    cudaError_t e = enqueue_steps(ctx, nsteps, ctx->parity, ctx->cur, &kl, &rec);
+    ctx->launches += kl;
+    cudaError_t es = cudaStreamSynchronize(ctx->st);
+    const int ncls = ctx->solver == RBF_SOLVER_ACM ? 4 : 1;
+    double sum[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    for (int i = 0; i < rec.count && e == cudaSuccess && es == cudaSuccess; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+            sum[cls[i]] += ms;
+            ++cnt[cls[i]];
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rbf_profile_steps launch");
+    if (es != cudaSuccess) return cuda_fail(ctx, es, "rbf_profile_steps sync");
+    for (int c = 0; c < ncls; ++c) kernel_ms[c] = cnt[c] ? sum[c] / cnt[c] : 0.0;
+    if (n_classes) *n_classes = ncls;
+    return RBF_OK;
+}
+
 int rbf_get_fields(rbf_ctx *ctx, double *uvwp) {
     if (!ctx || !uvwp) return RBF_EINVAL;
     if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_get_fields: not initialised");
     DeviceGuard dg(ctx->device);
-    DevArr<double> out;
-    CK(out.alloc(4 * ctx->n));
+    DevArr<double> &out = ctx->stage;
     if (ctx->solver == RBF_SOLVER_ACM) {
         if (ctx->prec == RBF_FP32) CK(launch_acm_export<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, out.p, ctx->st));
         else CK(launch_acm_export<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, out.p, ctx->st));
@@ -711,8 +765,7 @@ int rbf_set_fields(rbf_ctx *ctx, const double *uvwp) {
     if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_set_fields: not initialised");
     if (ctx->solver != RBF_SOLVER_ACM) return fail(ctx, RBF_EINVAL, "rbf_set_fields: ACM only (use rbf_lbm_set_populations)");
     DeviceGuard dg(ctx->device);
-    DevArr<double> in;
-    CK(in.alloc(4 * ctx->n));
+    DevArr<double> &in = ctx->stage;
     CK(cudaMemcpyAsync(in.p, uvwp, 4 * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     const int slot = (ctx->parity + 1) & 1;  // read by the next pressure sweep
     if (ctx->prec == RBF_FP32) {
@@ -731,12 +784,11 @@ int rbf_lbm_get_populations(rbf_ctx *ctx, double *f) {
     if (!ctx || !f) return RBF_EINVAL;
     if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_get_populations: no LBM state");
     DeviceGuard dg(ctx->device);
-    DevArr<double> out;
-    CK(out.alloc((size_t)ctx->q * ctx->n));
+    DevArr<double> &out = ctx->stage;
     if (ctx->prec == RBF_FP32) CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
     else CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
     ++ctx->launches;
-    CK(cudaMemcpyAsync(f, out.p, out.n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(f, out.p, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return RBF_OK;
 }
@@ -745,9 +797,8 @@ int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f) {
     if (!ctx || !f) return RBF_EINVAL;
     if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_set_populations: no LBM state");
     DeviceGuard dg(ctx->device);
-    DevArr<double> in;
-    CK(in.alloc((size_t)ctx->q * ctx->n));
-    CK(cudaMemcpyAsync(in.p, f, in.n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    DevArr<double> &in = ctx->stage;
+    CK(cudaMemcpyAsync(in.p, f, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     if (ctx->prec == RBF_FP32) CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
     else CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
     ++ctx->launches;

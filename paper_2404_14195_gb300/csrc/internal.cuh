@@ -34,6 +34,20 @@ struct OpSpec {
     double off[3];
 };
 
+// Records a CUDA event pair around each kernel launch (eager launches only) and
+// the kernel class of each pair, for per-launch device timing.
+struct LaunchRecorder {
+    cudaEvent_t *ev = nullptr;  // 2 * cap events
+    int *cls = nullptr;         // cap classes
+    int cap = 0, count = 0;
+    void begin(cudaStream_t st, int c) {
+        if (count < cap) { cudaEventRecord(ev[2 * count], st); cls[count] = c; }
+    }
+    void end(cudaStream_t st) {
+        if (count < cap) { cudaEventRecord(ev[2 * count + 1], st); ++count; }
+    }
+};
+
 // ---- launchers (all asynchronous on `st`; they return cudaGetLastError()) ----
 // knn.cu
 cudaError_t launch_morton_keys(int64_t n, const double *xyz, uint64_t *keys, int32_t *vals, int64_t npow,

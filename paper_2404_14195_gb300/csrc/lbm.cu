@@ -16,8 +16,9 @@
 // numbers (g_lb ~ 1e-9) the shift keeps the FP32 populations' significant bits on
 // the deviations instead of on omega_k.
 //
-// Layout: f~ SoA [q][n_pad]; stencil indices SELL [slice][j][lane]; weights SELL
-// [slice][k-1][j][lane] (k = 1..q-1), one node per lane.
+// Layout: f~ rest population [n_pad], then the (q-1)/2 opposite pairs
+// interleaved [pair][n_pad][2]; stencil indices SELL [slice][j][lane]; weights
+// SELL [slice][pair][j][lane][2], one node per lane.
 #include "lbm.cuh"
 
 namespace rbf {
@@ -54,6 +55,12 @@ double host_lattice_weight(int q, int k) { return q == 15 ? VSet<15>::w(k) : VSe
 
 // opposite of k: k+1 for odd k, k-1 for even k >= 2, 0 for 0
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// Population k of node i: the rest population in [0, npad), then the opposite
+// pairs (k, k') = (2p+1, 2p+2) interleaved, pair p at npad + 2 (p npad + i) + {0, 1}.
+__host__ __device__ __forceinline__ int64_t pop_at(int k, int64_t i, int64_t npad) {
+    return k == 0 ? i : npad + 2 * ((int64_t)((k - 1) >> 1) * npad + i) + ((k - 1) & 1);
+}
 
 // unknown-population masks of the wall nodes: bit k set when e_k . n > 0
 template <int Q>
@@ -109,8 +116,15 @@ __device__ __forceinline__ void trt_collide(T (&f)[Q], T tp_inv, T tm_inv, T gx,
     }
 }
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// One thread per node: all q populations of the node in registers.
 template <typename T, int Q>
 __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
+    using V = typename Vec2<T>::type;
+    constexpr int NP = (Q - 1) / 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int64_t s = i >> 5;
@@ -118,17 +132,22 @@ __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
     const int n_l = a.n_l;
     const int64_t np = a.npad;
     const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
-    const T *__restrict__ wp = a.w + ((s * (Q - 1) * (int64_t)n_l) << 5) + lane;
-    const T *__restrict__ fin = a.fin;
+    const V *__restrict__ wp = reinterpret_cast<const V *>(a.w) + ((s * NP * (int64_t)n_l) << 5) + lane;
+    const V *__restrict__ fp2 = reinterpret_cast<const V *>(a.fin + np);
     T f[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) f[k] = (T)0;
     for (int j = 0; j < n_l; ++j) {
         const int q = __ldg(ip + (j << 5));
 #pragma unroll
-        for (int k = 1; k < Q; ++k) f[k] += __ldg(wp + (((k - 1) * n_l + j) << 5)) * fin[k * np + q];
+        for (int p = 0; p < NP; ++p) {
+            const V w2 = __ldcs(wp + ((p * n_l + j) << 5));
+            const V g2 = __ldg(fp2 + p * np + q);
+            f[2 * p + 1] += w2.x * g2.x;
+            f[2 * p + 2] += w2.y * g2.y;
+        }
     }
-    f[0] = fin[i];
+    f[0] = a.fin[i];
     const uint32_t m = a.mask[i];
     if (m) {
 #pragma unroll
@@ -136,8 +155,113 @@ __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
             if (m & (1u << k)) f[k] = f[opp(k)];
     }
     trt_collide<T, Q>(f, a.tp_inv, a.tm_inv, a.gx, a.gy, a.gz);
+    a.fout[i] = f[0];
+    V *__restrict__ op2 = reinterpret_cast<V *>(a.fout + np);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) a.fout[k * np + i] = f[k];
+    for (int p = 0; p < NP; ++p) {
+        V o;
+        o.x = f[2 * p + 1];
+        o.y = f[2 * p + 2];
+        op2[p * np + i] = o;
+    }
+}
+
+// Pair-per-warp variant.  A block owns one SELL slice (32 nodes, one per lane)
+// and has (q-1)/2 warps; warp w handles the opposite pair (k, k') = (2w+1, 2w+2)
+// of every node, so the streaming of a pair, its bounce-back (which only swaps
+// within the pair) and its TRT update (which only couples the pair) stay in one
+// thread.  The moments are the only coupling between pairs: each warp writes its
+// partial (rho, momentum) to shared memory and every thread sums the partials in
+// the same order.  Warp 0 also carries the rest population.  The slice's stencil
+// indices are staged in shared memory once per block.  Pairs are interleaved in
+// memory (populations and weights), so each stencil column costs one 8-byte
+// gather and one 256-byte coalesced weight row per warp; the loop is unrolled U
+// deep to keep U such requests in flight per thread.
+template <typename T, int Q, int U>
+__global__ void __launch_bounds__(32 * ((Q - 1) / 2), sizeof(T) == 4 ? 5 : 2) k_lbm_step_pairs(LbmArgs<T> a) {
+    using V = typename Vec2<T>::type;
+    constexpr int NP = (Q - 1) / 2;
+    __shared__ int32_t sidx[RBF_MAX_NL][32];
+    __shared__ T part[NP][4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = 2 * w + 1, kb = k + 1;
+    const int64_t s = blockIdx.x;
+    const int64_t i = (s << 5) + lane;
+    const bool live = i < a.n;
+    const int n_l = a.n_l;
+    const int64_t np = a.npad;
+    {
+        const int32_t *__restrict__ src = a.idx + ((s * n_l) << 5);
+        for (int t = threadIdx.x; t < (n_l << 5); t += blockDim.x) sidx[t >> 5][t & 31] = __ldg(src + t);
+    }
+    __syncthreads();
+    const V *__restrict__ wp = reinterpret_cast<const V *>(a.w) + (((s * NP + w) * (int64_t)n_l) << 5) + lane;
+    const V *__restrict__ fp2 = reinterpret_cast<const V *>(a.fin + np) + (int64_t)w * np;
+    T ak = 0, ab = 0, f0 = 0;
+    if (live) {
+        int j = 0;
+        for (; j + U <= n_l; j += U) {
+            int q[U];
+            V w2[U], g2[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) q[u] = sidx[j + u][lane];
+#pragma unroll
+            for (int u = 0; u < U; ++u) w2[u] = __ldcs(wp + ((j + u) << 5));
+#pragma unroll
+            for (int u = 0; u < U; ++u) g2[u] = __ldg(fp2 + q[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                ak += w2[u].x * g2[u].x;
+                ab += w2[u].y * g2[u].y;
+            }
+        }
+        for (; j < n_l; ++j) {
+            const V w1 = __ldcs(wp + (j << 5));
+            const V g1 = __ldg(fp2 + sidx[j][lane]);
+            ak += w1.x * g1.x;
+            ab += w1.y * g1.y;
+        }
+        const uint32_t m = a.mask[i];
+        if (m & (1u << k)) ak = ab;
+        else if (m & (1u << kb)) ab = ak;
+        if (w == 0) f0 = a.fin[i];
+    }
+    const T ex = (T)VSet<Q>::e(k, 0), ey = (T)VSet<Q>::e(k, 1), ez = (T)VSet<Q>::e(k, 2);
+    const T dif = ak - ab;
+    part[w][0][lane] = ak + ab + f0;
+    part[w][1][lane] = ex * dif;
+    part[w][2][lane] = ey * dif;
+    part[w][3][lane] = ez * dif;
+    __syncthreads();
+    T drho = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+        drho += part[t][0][lane];
+        mx += part[t][1][lane];
+        my += part[t][2][lane];
+        mz += part[t][3][lane];
+    }
+    if (!live) return;
+    const T rho = (T)1 + drho;
+    const T vx = mx / rho, vy = my / rho, vz = mz / rho;
+    const T vv = vx * vx + vy * vy + vz * vz;
+    const T base = rho * ((T)-1.5 * vv);
+    const T tp_inv = a.tp_inv, tm_inv = a.tm_inv;
+    const T wk = (T)VSet<Q>::w(k);
+    const T eu = ex * vx + ey * vy + ez * vz;
+    const T eqp = wk * (drho + base + rho * ((T)4.5 * eu * eu));
+    const T eqm = wk * rho * ((T)3 * eu);
+    const T fp = (T)0.5 * (ak + ab), fm = (T)0.5 * (ak - ab);
+    const T dp = (fp - eqp) * tp_inv, dm = (fm - eqm) * tm_inv;
+    const T F = wk * (T)3 * rho * (ex * a.gx + ey * a.gy + ez * a.gz);
+    V o;
+    o.x = ak - dp - dm + F;
+    o.y = ab - dp + dm - F;
+    reinterpret_cast<V *>(a.fout + np)[(int64_t)w * np + i] = o;
+    if (w == 0) {
+        const T feq0 = (T)VSet<Q>::w(0) * (drho + base);
+        a.fout[i] = f0 - (f0 - feq0) * tp_inv;
+    }
 }
 
 // initial state: the collision of f_eq(rho = 1, v = 0) is f_eq + F_k, i.e.
@@ -151,7 +275,7 @@ __global__ void k_lbm_init(LbmArgs<T> a) {
     for (int k = 0; k < Q; ++k) f[k] = (T)0;
     trt_collide<T, Q>(f, a.tp_inv, a.tm_inv, a.gx, a.gy, a.gz);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) a.fout[k * a.npad + i] = i < a.n ? f[k] : (T)0;
+    for (int k = 0; k < Q; ++k) a.fout[pop_at(k, i, a.npad)] = i < a.n ? f[k] : (T)0;
 }
 
 // populations <-> FP64 unshifted, caller's order (perm: sorted -> caller)
@@ -161,7 +285,7 @@ __global__ void k_lbm_export(int64_t n, int64_t npad, const T *__restrict__ f, c
     if (i >= n) return;
     int64_t o = perm[i];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) out[k * n + o] = (double)f[k * npad + i] + VSet<Q>::w(k);
+    for (int k = 0; k < Q; ++k) out[k * n + o] = (double)f[pop_at(k, i, npad)] + VSet<Q>::w(k);
 }
 template <typename T, int Q>
 __global__ void k_lbm_import(int64_t n, int64_t npad, T *f, const int32_t *__restrict__ perm, const double *in) {
@@ -169,7 +293,7 @@ __global__ void k_lbm_import(int64_t n, int64_t npad, T *f, const int32_t *__res
     if (i >= n) return;
     int64_t o = perm[i];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) f[k * npad + i] = (T)(in[k * n + o] - VSet<Q>::w(k));
+    for (int k = 0; k < Q; ++k) f[pop_at(k, i, npad)] = (T)(in[k * n + o] - VSet<Q>::w(k));
 }
 
 // macroscopic fields from the post-collision state: rho is unchanged by the
@@ -182,7 +306,7 @@ __global__ void k_lbm_macro(int64_t n, int64_t npad, const T *__restrict__ f, do
     double d = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        double fk = (double)f[k * npad + i];
+        double fk = (double)f[pop_at(k, i, npad)];
         d += fk;
         mx += VSet<Q>::e(k, 0) * fk; my += VSet<Q>::e(k, 1) * fk; mz += VSet<Q>::e(k, 2) * fk;
     }
@@ -193,12 +317,49 @@ __global__ void k_lbm_macro(int64_t n, int64_t npad, const T *__restrict__ f, do
     out[4 * i + 3] = d;
 }
 
+// FP64 row weights w[c][k-1][j] -> paired SELL [slice][pair][j][lane][2] in T
 template <typename T>
-cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st) {
-    unsigned g = (unsigned)((a.n + 255) / 256);
-    if (q == 19) k_lbm_step<T, 19><<<g, 256, 0, st>>>(a);
-    else if (q == 15) k_lbm_step<T, 15><<<g, 256, 0, st>>>(a);
-    else return cudaErrorInvalidValue;
+__global__ void k_pack_pairs(int64_t nc, int npair, int n_l, const double *__restrict__ w, T *ws) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t npad = (nc + 31) & ~31LL;
+    if (t >= npad * n_l) return;
+    int64_t c = t / n_l;
+    int j = (int)(t - c * n_l);
+    int64_t s = c >> 5;
+    int lane = (int)(c & 31);
+    for (int p = 0; p < npair; ++p) {
+        int64_t e = ((((s * npair + p) * (int64_t)n_l + j) << 5) + lane) * 2;
+        ws[e] = c < nc ? (T)w[(c * 2 * npair + 2 * p) * n_l + j] : (T)0;
+        ws[e + 1] = c < nc ? (T)w[(c * 2 * npair + 2 * p + 1) * n_l + j] : (T)0;
+    }
+}
+
+cudaError_t lbm_launch_pack_f32(int64_t nc, int q, int n_l, const double *w, float *ws, cudaStream_t st) {
+    int64_t tot = ((nc + 31) & ~31LL) * n_l;
+    if (tot == 0) return cudaSuccess;
+    k_pack_pairs<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nc, (q - 1) / 2, n_l, w, ws);
+    return cudaGetLastError();
+}
+cudaError_t lbm_launch_pack_f64(int64_t nc, int q, int n_l, const double *w, double *ws, cudaStream_t st) {
+    int64_t tot = ((nc + 31) & ~31LL) * n_l;
+    if (tot == 0) return cudaSuccess;
+    k_pack_pairs<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nc, (q - 1) / 2, n_l, w, ws);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int variant) {
+    if (variant == LBM_NODE_PER_THREAD) {
+        unsigned g = (unsigned)((a.n + 255) / 256);
+        if (q == 19) k_lbm_step<T, 19><<<g, 256, 0, st>>>(a);
+        else if (q == 15) k_lbm_step<T, 15><<<g, 256, 0, st>>>(a);
+        else return cudaErrorInvalidValue;
+    } else {
+        unsigned g = (unsigned)(a.npad >> 5);
+        if (q == 19) k_lbm_step_pairs<T, 19, 5><<<g, 32 * 9, 0, st>>>(a);
+        else if (q == 15) k_lbm_step_pairs<T, 15, 5><<<g, 32 * 7, 0, st>>>(a);
+        else return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -242,7 +403,7 @@ cudaError_t lbm_launch_macro(int64_t n, int64_t npad, int q, const T *f, const d
 }
 
 #define RBF_LBM_INST(T)                                                                                         \
-    template cudaError_t lbm_launch_step<T>(const LbmArgs<T> &, int, cudaStream_t);                             \
+    template cudaError_t lbm_launch_step<T>(const LbmArgs<T> &, int, cudaStream_t, int);                        \
     template cudaError_t lbm_launch_init<T>(const LbmArgs<T> &, int, cudaStream_t);                             \
     template cudaError_t lbm_launch_export<T>(int64_t, int64_t, int, const T *, const int32_t *, double *,      \
                                               cudaStream_t);                                                    \

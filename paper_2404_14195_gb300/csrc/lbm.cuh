@@ -9,9 +9,9 @@ struct LbmArgs {
     int64_t n, npad;
     int n_l;
     const int32_t *idx;    // SELL [slice][j][lane]
-    const T *w;            // SELL [slice][k-1][j][lane], k = 1..q-1
+    const T *w;            // SELL [slice][pair][j][lane][2]
     const uint32_t *mask;  // unknown populations of wall nodes (bit k)
-    const T *fin;          // f~_post, [q][npad]
+    const T *fin;          // f~_post: rest [npad], pairs [(q-1)/2][npad][2]
     T *fout;
     T tp_inv, tm_inv;      // 1/tau+, 1/tau-
     T gx, gy, gz;          // g_lb
@@ -20,8 +20,12 @@ struct LbmArgs {
 const int *host_velocity_set(int q);
 double host_lattice_weight(int q, int k);
 
+// kernel variants of the fused step
+enum { LBM_NODE_PER_THREAD = 0, LBM_PAIR_PER_WARP = 1 };
 template <typename T>
-cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st);
+cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int variant = LBM_PAIR_PER_WARP);
+cudaError_t lbm_launch_pack_f32(int64_t nc, int q, int n_l, const double *w, float *ws, cudaStream_t st);
+cudaError_t lbm_launch_pack_f64(int64_t nc, int q, int n_l, const double *w, double *ws, cudaStream_t st);
 template <typename T>
 cudaError_t lbm_launch_init(const LbmArgs<T> &a, int q, cudaStream_t st);
 cudaError_t lbm_launch_masks(int64_t n, int q, const uint8_t *type, const double *nrm, uint32_t *mask, cudaStream_t st);

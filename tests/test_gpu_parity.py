@@ -136,11 +136,12 @@ def _lbm_case(rbf, cell, q, prec, g_phys, n_l=25):
     return s, u, idx, wk, dx
 
 
-@pytest.mark.parametrize("q", [19, 15])
-def test_lbm_fp64_populations(rbf, cell, q):
+@pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0)])
+def test_lbm_fp64_populations(rbf, cell, q, variant):
     # g large enough that f - omega is far above rounding (parity of the arithmetic)
     g = (2e4, 5e3, 0.0)
     s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP64, g)
+    s.set_kernel_variant(variant)
     tm = oracle.tau_minus(0.8, 3.0 / 16.0)
     f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
     n = 60
@@ -158,10 +159,12 @@ def test_lbm_fp64_populations(rbf, cell, q):
     assert rel_inf(fields[:, 3], p_want) <= 1e-8
 
 
-def test_lbm_fp32_populations(rbf, cell):
+@pytest.mark.parametrize("variant", [1, 0])
+def test_lbm_fp32_populations(rbf, cell, variant):
     q = 19
     g = (2e4, 5e3, 0.0)
     s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP32, g)
+    s.set_kernel_variant(variant)
     tm = oracle.tau_minus(0.8, 3.0 / 16.0)
     f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
     n = 60

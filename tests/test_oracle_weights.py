@@ -48,6 +48,18 @@ def test_knn_matches_brute_force(cell):
     assert np.array_equal(idx[:, 0], np.arange(len(xyz)))
 
 
+def test_grid_knn_equals_brute_force():
+    rc = synth.refined_cell(r=0.3, h_min=0.02, h_max=0.06, ramp=0.2, seed=4)
+    xyz = rc["xyz"]
+    rng = np.random.default_rng(1)
+    q = np.concatenate([xyz[::7], rng.random((300, 3))])
+    for n_l in (25, 40):
+        assert np.array_equal(oracle.knn(xyz, q, n_l, grid=True), oracle.knn(xyz, q, n_l, grid=False))
+    lat = synth.lattice(7)
+    assert np.array_equal(oracle.knn(lat["xyz"], lat["xyz"], 27, grid=True),
+                          oracle.knn(lat["xyz"], lat["xyz"], 27, grid=False))
+
+
 def test_knn_free_points_and_ties():
     # exact lattice: many equal distances; order must follow the node index
     lat = synth.lattice(6)
