@@ -200,6 +200,26 @@ int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
 
+/* Permeability exactly as rbf_permeability(m_p), for callers that cannot allocate
+ * device memory at this point: for example code whose device memory is owned by
+ * another allocator (a framework's caching pool, or an arena sized at start-up
+ * that leaves nothing for cudaMalloc), or a loop in which the device-wide
+ * synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has no
+ * counterpart; this is a deployment variant of the probe reduction.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *  - Its scratch (block partials and the sum) is one static device array of
+ *    4097 doubles that every GPU loading the library holds until exit; the
+ *    probe set must already exist: call rbf_permeability(ctx, m_p, ...) once
+ *    first (it builds the probes, which allocates), else RBF_EINVAL.
+ *  - At most 1,048,576 fluid probes; more returns RBF_EINVAL.
+ *  - The first call on a device looks up the scratch address for that device;
+ *    make that first call before any stream capture.
+ *  - All calls share the one array, so calls that overlap on the GPU (other
+ *    contexts or streams on the same device) race; serialise them.  Each call
+ *    overwrites the partials it uses, so nothing needs clearing.
+ *  - Writes *k_over_d2 and *q (either may be NULL) before returning. */
+int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q);
+
 #ifdef __cplusplus
 }
 #endif

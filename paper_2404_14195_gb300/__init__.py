@@ -88,6 +88,7 @@ ABI = {
     "rbf_launch_count": (_I64, [_P]),
     "rbf_profile_steps": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "rbf_set_kernel_variant": (_I, [_P, _I]),
+    "rbf_permeability_static": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
 }
 
 
@@ -232,6 +233,13 @@ class Solver:
     def permeability(self, m_p: int = 32):
         k, q = ctypes.c_double(), ctypes.c_double()
         self._ck(self._L.rbf_permeability(self._h, m_p, ctypes.byref(k), ctypes.byref(q)))
+        return k.value, q.value
+
+    def permeability_static(self, m_p: int = 32):
+        """As permeability(m_p) without any device allocation (static scratch);
+        needs a prior permeability(m_p) call that built the probe set."""
+        k, q = ctypes.c_double(), ctypes.c_double()
+        self._ck(self._L.rbf_permeability_static(self._h, m_p, ctypes.byref(k), ctypes.byref(q)))
         return k.value, q.value
 
     def drag(self, m_p: int = 32):

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -988,3 +989,102 @@ int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Permeability without device allocation.
+//
+// rbf_permeability keeps its per-block partial sums in a buffer the context
+// allocated.  rbf_permeability_static runs a copy of the same probe reduction
+// whose partials and result live in the file-scope array below instead, so the
+// call itself allocates no device memory.  Host code cannot use the array's name
+// as a device address (it names a host-side stand-in), so its address is looked
+// up with cudaGetSymbolAddress once per device, with that device current, the
+// first time the entry point runs on it.
+#define RBF_STATIC_FLUX_BLOCKS 4096  // up to 4096 * 256 = 1,048,576 fluid probes
+static __device__ __align__(256) double g_static_flux[RBF_STATIC_FLUX_BLOCKS + 32];
+static double *g_static_flux_addr[64] = {nullptr};
+static std::mutex g_static_flux_mu;
+
+namespace {
+
+cudaError_t static_flux_scratch(int device, double **out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_flux_mu);
+    if (!g_static_flux_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_flux);  // the device is current (DeviceGuard)
+        if (e != cudaSuccess) return e;
+        g_static_flux_addr[device] = (double *)p;
+    }
+    *out = g_static_flux_addr[device];
+    return cudaSuccess;
+}
+
+// block b writes its partial to scratch[b]; every launch overwrites the partials of
+// the blocks it runs, so nothing has to start at zero
+template <typename T>
+__global__ void __launch_bounds__(256) k_probe_sum_static(int64_t np, int n_l, const int32_t *idx, const double *w,
+                                                          const T *vx, int64_t stride, double *scratch) {
+    __shared__ double red[8];
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (p < np)
+        for (int j = 0; j < n_l; ++j) s += w[p * n_l + j] * (double)vx[idx[p * n_l + j] * stride];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        scratch[blockIdx.x] = t;
+    }
+}
+
+// fixed-order sum of nb partials into scratch[RBF_STATIC_FLUX_BLOCKS]
+__global__ void k_static_final(double *scratch, int64_t nb) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nb; b += 32) s += scratch[b];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) scratch[RBF_STATIC_FLUX_BLOCKS] = s;
+}
+
+}  // namespace
+
+extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_permeability_static: not initialised");
+    if (ctx->m_p != m_p || !ctx->pidx.p)
+        return fail(ctx, RBF_EINVAL, "rbf_permeability_static: build the probe set first with rbf_permeability(m_p)");
+    const int64_t nb = (ctx->np_fluid + 255) / 256;
+    if (nb > RBF_STATIC_FLUX_BLOCKS)
+        return fail(ctx, RBF_EINVAL, "rbf_permeability_static: more than 1,048,576 fluid probes (static scratch limit)");
+    DeviceGuard dg(ctx->device);
+    double *scratch = nullptr;
+    CK(static_flux_scratch(ctx->device, &scratch));
+    double s = 0.0;
+    if (nb > 0) {
+        if (ctx->solver == RBF_SOLVER_ACM) {
+            if (ctx->prec == RBF_FP32)
+                k_probe_sum_static<float><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, scratch);
+            else
+                k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, scratch);
+        } else {
+            if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+            else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+            ++ctx->launches;
+            k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, scratch);
+        }
+        k_static_final<<<1, 32, 0, ctx->st>>>(scratch, nb);
+        ctx->launches += 2;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&s, scratch + RBF_STATIC_FLUX_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    if (ctx->solver == RBF_SOLVER_LBM) s *= ctx->dx / ctx->lbm_dt;
+    const double qq = s / (5.0 * m_p * m_p);
+    const double *g = ctx->prm.g;
+    const double gmag = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (q) *q = qq;
+    if (k_over_d2) *k_over_d2 = gmag > 0.0 ? qq * ctx->prm.nu / gmag : 0.0;
+    return RBF_OK;
+}
