@@ -35,6 +35,8 @@ METRIC = "node-steps/s; time-to-steady-permeability (1e-4 rel) vs plain FP64 on 
 UNIT = "node-steps/s"
 R, H_MIN, H_MAX, RAMP, SEED = 0.40, 0.008, 0.04, 0.2, 2
 N_L, Q, DX, TAU_P, MAGIC = 30, 19, 0.004, 0.8, 3.0 / 16.0
+KERNELS = {0: "k_lbm_step<float,19> (256)", 1: "k_lbm_step_pairs<float,19,5>", 2: "k_lbm_step<float,19> (128)",
+           3: "k_lbm_step_pairs<float,19,3>", 4: "k_lbm_step_pairs<float,19,6>", 5: "k_lbm_step_pairs<float,19,2>"}
 
 
 def workload():
@@ -116,13 +118,14 @@ def measured_peaks():
         return None
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the fused LBM kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+def kernel_traffic(kernel):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    valid only for that kernel and while its source is unchanged."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "lbm_step_traffic.json")))
         src = open(os.path.join(ROOT, "paper_2404_14195_gb300", "csrc", "lbm.cu"), "rb").read()
-        if rec.get("lbm_cu_sha256") == hashlib.sha256(src).hexdigest() and rec.get("nodes_full"):
+        if (rec.get("lbm_cu_sha256") == hashlib.sha256(src).hexdigest() and rec.get("nodes_full")
+                and rec.get("bench_kernel") == kernel):
             return rec["dram_bytes_per_launch_full"]
     except Exception:
         pass
@@ -185,7 +188,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
-    ap.add_argument("--variant", type=int, default=1, help="LBM kernel: 0 node per thread, 1 pair per warp")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="LBM step schedule (rbf_set_kernel_variant code); -1 = autotune on the case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,7 +214,12 @@ def main():
     s.build_stencils(N_L)
     s.compute_weights(k=3, m=2, solver=rbf.RBF_SOLVER_LBM, q=Q, dx=DX)
     s.init(precision=rbf.RBF_FP32, nu=1.0, g=(1.0, 0.0, 0.0), tau_plus=TAU_P, magic=MAGIC)
-    s.set_kernel_variant(args.variant)
+    tune = None
+    if args.variant >= 0:
+        s.set_kernel_variant(args.variant)
+        chosen = args.variant
+    else:
+        tune, chosen = s.autotune(40)
     s.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -274,8 +283,9 @@ def main():
         "dtype": "f32", "data": "synthetic (seeded node cloud; the paper's datasets are not used)",
         "config": config_dict(n, nb) | {"parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic(),
-                     "kernel": ["k_lbm_step<float,19>", "k_lbm_step_pairs<float,19,5>"][args.variant],
+                     "traffic": kernel_traffic(KERNELS[chosen]),
+                     "kernel": KERNELS[chosen],
+                     "schedule": chosen, "autotune_ms_per_step": tune,
                      "bytes_per_launch": bpl,
                      "per_launch_ms_timed_region": per_launch_ms, "per_launch_ms_event_pairs": prof_ms,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback"},

@@ -191,11 +191,28 @@ int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int6
  * correction).  kernel_ms must hold 4 doubles.  1 <= nsteps <= 4096. */
 int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classes);
 
-/* Kernel variant of the fused LBM step: 0 one node per thread (all q
- * populations of a node in one thread); 1 one opposite-population pair per warp
- * (q-1)/2 warps per 32-node slice, moments reduced in shared memory (default).
- * Both compute the same step; the choice only changes the schedule. */
+/* Schedule of the fused LBM step (all compute the same step; only the thread
+ * mapping differs): 0 one node per thread, 256-thread blocks; 1 one opposite-
+ * population pair per warp, (q-1)/2 warps per 32-node slice, moments reduced in
+ * shared memory, stencil loop unrolled 5 deep (default); 2 as 0 with 128-thread
+ * blocks; 3, 4, 5 as 1 unrolled 3, 6, 2 deep. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
+
+typedef struct {
+    int solver;          /* RBF_SOLVER_ACM or RBF_SOLVER_LBM */
+    int n_candidates;
+    int code[8];         /* LBM: schedule codes of rbf_set_kernel_variant; ACM: threads per block */
+    double ms_per_step[8];
+    int chosen;          /* the fastest candidate, now in use */
+} rbf_tune_report;
+
+/* Autotuner: time every candidate schedule of the step kernels on this
+ * context's own case (LBM: the six fused-step schedules; ACM: 256, 128 and 64
+ * threads per block for the sweeps), trial_steps steps each with CUDA events on
+ * the context stream, keep the fastest.  The fields are saved before and restored
+ * after the trials, so the state and step count are unchanged.  Needs rbf_init;
+ * allocates a temporary copy of the state.  2 <= trial_steps <= 2000. */
+int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);

@@ -50,6 +50,11 @@ class rbf_params(ctypes.Structure):
                 ("tau_plus", ctypes.c_double), ("magic", ctypes.c_double)]
 
 
+class rbf_tune_report(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("n_candidates", ctypes.c_int), ("code", ctypes.c_int * 8),
+                ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int)]
+
+
 class rbf_solve_opts(ctypes.Structure):
     _fields_ = [("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
                 ("m_p", ctypes.c_int)]
@@ -89,6 +94,7 @@ ABI = {
     "rbf_profile_steps": (_I, [_P, _I, _P, ctypes.POINTER(_I)]),
     "rbf_set_kernel_variant": (_I, [_P, _I]),
     "rbf_permeability_static": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "rbf_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
 }
 
 
@@ -271,8 +277,16 @@ class Solver:
         return ms[:nc.value].copy()
 
     def set_kernel_variant(self, variant: int):
-        """0: one node per thread; 1: one population pair per warp (default)."""
+        """LBM step schedule: 0 / 2 one node per thread (256 / 128 threads per
+        block); 1 / 3 / 4 / 5 one population pair per warp, unrolled 5 / 3 / 6 / 2."""
         self._ck(self._L.rbf_set_kernel_variant(self._h, int(variant)))
+
+    def autotune(self, trial_steps: int = 50):
+        """Time the candidate step schedules on this case and keep the fastest;
+        the state is restored afterwards.  Returns {code: ms_per_step}, chosen."""
+        r = rbf_tune_report()
+        self._ck(self._L.rbf_autotune(self._h, int(trial_steps), ctypes.byref(r)))
+        return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
 
     def launch_count(self) -> int:
         return int(self._L.rbf_launch_count(self._h))

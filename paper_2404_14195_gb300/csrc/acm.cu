@@ -144,11 +144,12 @@ __global__ void k_acm_vmax(AcmArgs<T> a, int slot) {
 // iteration's) and clears slot g % 2 for its own correction sweep.
 template <typename T>
 cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                            LaunchRecorder *rec) {
-    const unsigned gb = (unsigned)((a.n + 255) / 256);
+                            LaunchRecorder *rec, int block) {
+    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+    const unsigned gb = (unsigned)((a.n + block - 1) / block);
     const unsigned gw = (unsigned)((a.nb + 255) / 256);
     if (rec) rec->begin(st, 0);
-    k_acm_predict<T><<<gb, 256, 0, st>>>(a);
+    k_acm_predict<T><<<gb, block, 0, st>>>(a);
     if (rec) rec->end(st);
     ++*launches;
     for (int it = 0; it < n_p; ++it) {
@@ -157,7 +158,7 @@ cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream
         const T *w = it == 0 ? a.ws : a.w_;
         const int g = (parity + it) & 1;
         if (rec) rec->begin(st, 1);
-        k_acm_pressure<T><<<gb, 256, 0, st>>>(a, u, v, w, g ^ 1, g);
+        k_acm_pressure<T><<<gb, block, 0, st>>>(a, u, v, w, g ^ 1, g);
         if (rec) rec->end(st);
         ++*launches;
         if (a.nb > 0) {
@@ -167,7 +168,7 @@ cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream
             ++*launches;
         }
         if (rec) rec->begin(st, 3);
-        k_acm_correct<T><<<gb, 256, 0, st>>>(a, g);
+        k_acm_correct<T><<<gb, block, 0, st>>>(a, g);
         if (rec) rec->end(st);
         ++*launches;
     }
@@ -188,8 +189,8 @@ cudaError_t acm_launch_predict_only(const AcmArgs<T> &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template cudaError_t acm_launch_step<float>(const AcmArgs<float> &, int, int, cudaStream_t, int64_t *, LaunchRecorder *);
-template cudaError_t acm_launch_step<double>(const AcmArgs<double> &, int, int, cudaStream_t, int64_t *, LaunchRecorder *);
+template cudaError_t acm_launch_step<float>(const AcmArgs<float> &, int, int, cudaStream_t, int64_t *, LaunchRecorder *, int);
+template cudaError_t acm_launch_step<double>(const AcmArgs<double> &, int, int, cudaStream_t, int64_t *, LaunchRecorder *, int);
 template cudaError_t acm_launch_vmax<float>(const AcmArgs<float> &, int, cudaStream_t);
 template cudaError_t acm_launch_vmax<double>(const AcmArgs<double> &, int, cudaStream_t);
 template cudaError_t acm_launch_predict_only<float>(const AcmArgs<float> &, cudaStream_t);

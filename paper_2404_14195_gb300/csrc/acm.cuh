@@ -23,7 +23,7 @@ struct AcmArgs {
 
 template <typename T>
 cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                            LaunchRecorder *rec = nullptr);
+                            LaunchRecorder *rec = nullptr, int block = 256);
 template <typename T>
 cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st);
 template <typename T>

@@ -93,7 +93,9 @@ struct rbf_ctx {
     // graph of `gsteps` steps
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1;
-    int variant = LBM_PAIR_PER_WARP;  // kernel variant of the step
+    int variant = LBM_PAIR_PER_WARP;  // schedule of the fused LBM step
+    int acm_block = 256;              // threads per block of the ACM sweeps
+    int gblock = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
     int64_t last_steps = 0;
@@ -234,8 +236,8 @@ cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
         if (ctx->solver == RBF_SOLVER_ACM) {
-            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec);
-            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec);
+            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
+            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
             parity = (parity + ctx->n_p) & 1;
         } else {
             if (rec) rec->begin(ctx->st, 0);
@@ -255,7 +257,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
     int64_t kl = 0;
     if (full > 0) {
         if (!ctx->gexec || ctx->gparity != ctx->parity || ctx->gcur != ctx->cur || ctx->gprec != ctx->prec ||
-            ctx->gsteps != chunk || ctx->gvariant != ctx->variant) {
+            ctx->gsteps != chunk || ctx->gvariant != ctx->variant || ctx->gblock != ctx->acm_block) {
             drop_graph(ctx);
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -273,6 +275,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
             ctx->gcur = ctx->cur;
             ctx->gprec = ctx->prec;
             ctx->gvariant = ctx->variant;
+            ctx->gblock = ctx->acm_block;
             ctx->last_kernel_launches = dummy;
         }
         int64_t per_graph = ctx->last_kernel_launches;
@@ -697,9 +700,97 @@ int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int6
 
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant) {
     if (!ctx) return RBF_EINVAL;
-    if (variant != LBM_NODE_PER_THREAD && variant != LBM_PAIR_PER_WARP)
-        return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: 0 or 1");
+    if (variant < 0 || variant >= LBM_N_SCHEDULES)
+        return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: schedule code out of range");
     ctx->variant = variant;
+    return RBF_OK;
+}
+
+namespace {
+// snapshot / restore of the stepping state around autotuning trials
+struct StateCopy {
+    std::vector<DevArr<char> *> bufs;
+    std::vector<std::pair<void *, size_t>> src;
+    ~StateCopy() { for (auto *b : bufs) delete b; }
+};
+int save_state(rbf_ctx *ctx, StateCopy &sc) {
+    auto add = [&](void *p, size_t bytes) -> cudaError_t {
+        if (!p || !bytes) return cudaSuccess;
+        auto *b = new DevArr<char>();
+        sc.bufs.push_back(b);
+        cudaError_t e = b->alloc(bytes);
+        if (e != cudaSuccess) return e;
+        sc.src.push_back({p, bytes});
+        return cudaMemcpyAsync(b->p, p, bytes, cudaMemcpyDeviceToDevice, ctx->st);
+    };
+    for (int i = 0; i < 10; ++i) {
+        CK(add(ctx->a32[i].p, ctx->a32[i].n * sizeof(float)));
+        CK(add(ctx->a64[i].p, ctx->a64[i].n * sizeof(double)));
+    }
+    for (int i = 0; i < 2; ++i) {
+        CK(add(ctx->f32[i].p, ctx->f32[i].n * sizeof(float)));
+        CK(add(ctx->f64[i].p, ctx->f64[i].n * sizeof(double)));
+    }
+    CK(add(ctx->vmax.p, ctx->vmax.n * sizeof(unsigned long long)));
+    return RBF_OK;
+}
+int restore_state(rbf_ctx *ctx, StateCopy &sc) {
+    for (size_t i = 0; i < sc.src.size(); ++i)
+        CK(cudaMemcpyAsync(sc.src[i].first, sc.bufs[i]->p, sc.src[i].second, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+}  // namespace
+
+int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_autotune: call rbf_init first");
+    if (trial_steps < 2 || trial_steps > 2000) return fail(ctx, RBF_EINVAL, "rbf_autotune: 2 <= trial_steps <= 2000");
+    DeviceGuard dg(ctx->device);
+    drop_graph(ctx);
+    const int par0 = ctx->parity, cur0 = ctx->cur, var0 = ctx->variant, blk0 = ctx->acm_block;
+    StateCopy sc;
+    int rc = save_state(ctx, sc);
+    if (rc) return rc;
+    std::vector<int> cands;
+    if (ctx->solver == RBF_SOLVER_LBM)
+        cands = {LBM_PAIR_PER_WARP, LBM_NODE_PER_THREAD, LBM_NODE_PER_THREAD_128, LBM_PAIR_PER_WARP_U3,
+                 LBM_PAIR_PER_WARP_U6, LBM_PAIR_PER_WARP_U2};
+    else
+        cands = {256, 128, 64};
+    rbf_tune_report r;
+    std::memset(&r, 0, sizeof(r));
+    double best = 1e300;
+    int best_code = cands[0];
+    for (size_t c = 0; c < cands.size() && c < 8; ++c) {
+        if (ctx->solver == RBF_SOLVER_LBM) ctx->variant = cands[c]; else ctx->acm_block = cands[c];
+        int64_t kl = 0;
+        int par = ctx->parity, cu = ctx->cur;
+        cudaError_t e = enqueue_steps(ctx, 2, par, cu, &kl);  // warm-up
+        CK(e);
+        CK(cudaEventRecord(ctx->ev0, ctx->st));
+        e = enqueue_steps(ctx, trial_steps, par, cu, &kl);
+        CK(e);
+        CK(cudaEventRecord(ctx->ev1, ctx->st));
+        CK(cudaEventSynchronize(ctx->ev1));
+        ctx->launches += kl;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        const double per = ms / trial_steps;
+        r.code[c] = cands[c];
+        r.ms_per_step[c] = per;
+        r.n_candidates = (int)c + 1;
+        if (per < best) { best = per; best_code = cands[c]; }
+        rc = restore_state(ctx, sc);
+        if (rc) return rc;
+    }
+    ctx->parity = par0;
+    ctx->cur = cur0;
+    (void)var0; (void)blk0;
+    if (ctx->solver == RBF_SOLVER_LBM) ctx->variant = best_code; else ctx->acm_block = best_code;
+    r.chosen = best_code;
+    r.solver = ctx->solver;
+    if (rep) *rep = r;
     return RBF_OK;
 }
 

@@ -347,20 +347,27 @@ cudaError_t lbm_launch_pack_f64(int64_t nc, int q, int n_l, const double *w, dou
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int variant) {
-    if (variant == LBM_NODE_PER_THREAD) {
-        unsigned g = (unsigned)((a.n + 255) / 256);
-        if (q == 19) k_lbm_step<T, 19><<<g, 256, 0, st>>>(a);
-        else if (q == 15) k_lbm_step<T, 15><<<g, 256, 0, st>>>(a);
-        else return cudaErrorInvalidValue;
-    } else {
-        unsigned g = (unsigned)(a.npad >> 5);
-        if (q == 19) k_lbm_step_pairs<T, 19, 5><<<g, 32 * 9, 0, st>>>(a);
-        else if (q == 15) k_lbm_step_pairs<T, 15, 5><<<g, 32 * 7, 0, st>>>(a);
-        else return cudaErrorInvalidValue;
+template <typename T, int Q>
+static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code) {
+    constexpr int NP = (Q - 1) / 2;
+    const unsigned slices = (unsigned)(a.npad >> 5);
+    switch (code) {
+    case LBM_NODE_PER_THREAD: k_lbm_step<T, Q><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a); break;
+    case LBM_NODE_PER_THREAD_128: k_lbm_step<T, Q><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP: k_lbm_step_pairs<T, Q, 5><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U3: k_lbm_step_pairs<T, Q, 3><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U6: k_lbm_step_pairs<T, Q, 6><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U2: k_lbm_step_pairs<T, Q, 2><<<slices, 32 * NP, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int code) {
+    if (q == 19) return launch_step_q<T, 19>(a, st, code);
+    if (q == 15) return launch_step_q<T, 15>(a, st, code);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

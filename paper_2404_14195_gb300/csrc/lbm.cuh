@@ -20,8 +20,13 @@ struct LbmArgs {
 const int *host_velocity_set(int q);
 double host_lattice_weight(int q, int k);
 
-// kernel variants of the fused step
-enum { LBM_NODE_PER_THREAD = 0, LBM_PAIR_PER_WARP = 1 };
+// schedules of the fused step (same arithmetic, different thread mapping):
+// node per thread with 256 / 128 threads per block; pair per warp with the
+// stencil loop unrolled 5 / 3 / 6 / 2 deep
+enum {
+    LBM_NODE_PER_THREAD = 0, LBM_PAIR_PER_WARP = 1, LBM_NODE_PER_THREAD_128 = 2,
+    LBM_PAIR_PER_WARP_U3 = 3, LBM_PAIR_PER_WARP_U6 = 4, LBM_PAIR_PER_WARP_U2 = 5, LBM_N_SCHEDULES = 6
+};
 template <typename T>
 cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int variant = LBM_PAIR_PER_WARP);
 cudaError_t lbm_launch_pack_f32(int64_t nc, int q, int n_l, const double *w, float *ws, cudaStream_t st);

@@ -136,7 +136,7 @@ def _lbm_case(rbf, cell, q, prec, g_phys, n_l=25):
     return s, u, idx, wk, dx
 
 
-@pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0)])
+@pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0), (19, 2), (19, 3), (19, 4), (15, 5)])
 def test_lbm_fp64_populations(rbf, cell, q, variant):
     # g large enough that f - omega is far above rounding (parity of the arithmetic)
     g = (2e4, 5e3, 0.0)
@@ -239,3 +239,37 @@ def test_errors_are_reported(rbf, cell):
     with pytest.raises(rbf.RbfError) as ei:
         s2.compute_weights(k=3, m=2)
     assert ei.value.code == rbf.RBF_ESINGULAR
+
+
+@pytest.mark.parametrize("solver", ["lbm", "acm"])
+def test_autotune_keeps_state_and_parity(rbf, cell, orc_acm, solver):
+    if solver == "lbm":
+        q, g = 19, (2e4, 5e3, 0.0)
+        s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP64, g)
+        s.step(7)
+        before = s.lbm_get_populations()
+        times, chosen = s.autotune(10)
+        assert len(times) == 6 and chosen in times
+        assert np.array_equal(s.lbm_get_populations(), before)
+        s.step(23)
+        tm = oracle.tau_minus(0.8, 3.0 / 16.0)
+        f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
+        fn = oracle.lbm_run(f0, q, cell, idx, wk, 0.8, tm, u["g_lb"], 30)
+        want = oracle.lbm_collide(fn, q, 0.8, tm, u["g_lb"])
+        _, om, _ = oracle.velocity_set(q)
+        assert rel_inf(s.lbm_get_populations() - om[:, None], want - om[:, None]) <= 1e-9
+    else:
+        s, _ = make_solver(rbf, cell, 25, rbf.RBF_SOLVER_ACM)
+        dt = oracle.acm_dt(orc_acm["h_min"], 1.0)
+        s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=0.01)
+        s.step(5)
+        before = s.get_fields()
+        times, chosen = s.autotune(10)
+        assert set(times) == {256, 128, 64} and chosen in times
+        assert np.array_equal(s.get_fields(), before)
+        s.step(25)
+        want, _ = oracle.acm_run(cell, orc_acm["idx"], orc_acm["w4"], orc_acm["idxb"], orc_acm["wgb"],
+                                 np.zeros((cell.n, 4)), 30, dt=dt, v_ref=0.01)
+        got = s.get_fields()
+        for c in range(4):
+            assert rel_inf(got[:, c], want[:, c]) <= 1e-9, c
