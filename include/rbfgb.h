@@ -217,6 +217,47 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
 
+/* ---- learned warm start ------------------------------------------------------
+ * The paper has no network; this is the build's warm start for the steady ACM
+ * solve.  A multilayer perceptron maps 34 features of a node (sin and cos of
+ * 2 pi n.x for 16 integer wave vectors n, periodic in the cell; the grain radius
+ * r; the signed wall distance phi_sdf) to (u, v, w, p) divided by |g| d^2 / nu.
+ * Layers 64 -> 128 -> 128 -> 128 -> 128 -> 16 (features zero-padded from 34 to 64,
+ * outputs 4..15 unused and held at zero), GELU (tanh form) after the first four.
+ * Forward and backward run as BF16 tensor-core GEMMs (tcgen05, FP32 accumulation
+ * in tensor memory); Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 masters.
+ * Loss: mean squared error over the 4 outputs.  Parameters are one FP32 vector:
+ * per layer W (fan_out x fan_in, row-major) then b (fan_out), layers in order. */
+typedef struct rbf_mlp rbf_mlp;
+int64_t rbf_mlp_num_params(void);
+int rbf_mlp_create(rbf_mlp **out, int device, void *cuda_stream);
+int rbf_mlp_destroy(rbf_mlp *mlp);
+const char *rbf_mlp_last_error(const rbf_mlp *mlp);
+/* Set / get the FP32 parameters (rbf_mlp_num_params() floats); set also resets
+ * the Adam moments and step counters. */
+int rbf_mlp_set_params(rbf_mlp *mlp, const float *theta);
+int rbf_mlp_get_params(rbf_mlp *mlp, float *theta);
+/* Training samples (copied): n node positions (n x 3), per-sample radius and wall
+ * distance, targets (n x 4, already divided by |g| d^2 / nu). */
+int rbf_mlp_set_data(rbf_mlp *mlp, int64_t n, const double *xyz, const float *radius, const float *sdf,
+                     const float *target);
+/* `steps` Adam steps on mini-batches of `batch` samples (a multiple of 128) drawn
+ * with the counter-based SplitMix64: sample = splitmix64(seed * 2^32 + s * batch +
+ * b) mod n for draw s (counted since rbf_mlp_set_params).  loss_hist (steps
+ * floats, may be NULL) receives each step's mean squared error.  Returns
+ * RBF_ETIMEOUT if a tensor-core wait exceeded its limit. */
+int rbf_mlp_train(rbf_mlp *mlp, int steps, int batch, double lr, uint64_t seed, float *loss_hist);
+/* Gradient (rbf_mlp_num_params() floats, packed like the parameters) and mean
+ * squared error of the given samples (batch a multiple of 128), no update. */
+int rbf_mlp_gradient(rbf_mlp *mlp, int batch, const int64_t *sample_idx, float *grad, double *loss);
+/* Network output for n points: out (n x 4) in the scaled units of the targets. */
+int rbf_mlp_predict(rbf_mlp *mlp, int64_t n, const double *xyz, const float *radius, const float *sdf, float *out);
+/* Warm start: write scale x the prediction at the context's nodes into its ACM
+ * fields (velocity zero on wall nodes) and recompute C of Eq. MNS_C.  The context
+ * must be an initialised ACM context with a sphere, on the same device. */
+int rbf_mlp_warm_start(rbf_mlp *mlp, rbf_ctx *ctx, double scale);
+int64_t rbf_mlp_launch_count(const rbf_mlp *mlp);
+
 /* Permeability exactly as rbf_permeability(m_p), for callers that cannot allocate
  * device memory at this point: for example code whose device memory is owned by
  * another allocator (a framework's caching pool, or an arena sized at start-up

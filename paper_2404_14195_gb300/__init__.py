@@ -95,6 +95,18 @@ ABI = {
     "rbf_set_kernel_variant": (_I, [_P, _I]),
     "rbf_permeability_static": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rbf_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
+    "rbf_mlp_num_params": (_I64, []),
+    "rbf_mlp_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "rbf_mlp_destroy": (_I, [_P]),
+    "rbf_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "rbf_mlp_set_params": (_I, [_P, _P]),
+    "rbf_mlp_get_params": (_I, [_P, _P]),
+    "rbf_mlp_set_data": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "rbf_mlp_train": (_I, [_P, _I, _I, _D, ctypes.c_uint64, _P]),
+    "rbf_mlp_gradient": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
+    "rbf_mlp_predict": (_I, [_P, _I64, _P, _P, _P, _P]),
+    "rbf_mlp_warm_start": (_I, [_P, _P, _D]),
+    "rbf_mlp_launch_count": (_I64, [_P]),
 }
 
 
@@ -290,3 +302,77 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(self._L.rbf_launch_count(self._h))
+
+
+class Mlp:
+    """The warm-start network (an ``rbf_mlp``): BF16 tensor-core forward,
+    backward and Adam on the GPU; parameters as one packed FP32 vector."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        rc = L.rbf_mlp_create(ctypes.byref(h), device, stream)
+        if rc != RBF_OK:
+            raise RbfError(rc, "rbf_mlp_create failed (no usable CUDA device?)")
+        self._h = h
+        self.n_params = int(L.rbf_mlp_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rbf_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc != RBF_OK:
+            raise RbfError(rc, self._L.rbf_mlp_last_error(self._h).decode())
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, np.float32)
+        assert t.size == self.n_params
+        self._ck(self._L.rbf_mlp_set_params(self._h, _ptr(t)))
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        self._ck(self._L.rbf_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_data(self, xyz, radius, sdf, target):
+        x = np.ascontiguousarray(xyz, np.float64)
+        r = np.ascontiguousarray(radius, np.float32)
+        s = np.ascontiguousarray(sdf, np.float32)
+        t = np.ascontiguousarray(target, np.float32)
+        self._keep = (x, r, s, t)
+        self._ck(self._L.rbf_mlp_set_data(self._h, len(x), _ptr(x), _ptr(r), _ptr(s), _ptr(t)))
+
+    def train(self, steps: int, batch: int, lr: float, seed: int):
+        hist = np.zeros(max(steps, 1), np.float32)
+        self._ck(self._L.rbf_mlp_train(self._h, int(steps), int(batch), float(lr), int(seed), _ptr(hist)))
+        return hist[:steps]
+
+    def gradient(self, sample_idx):
+        idx = np.ascontiguousarray(sample_idx, np.int64)
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        self._ck(self._L.rbf_mlp_gradient(self._h, len(idx), _ptr(idx), _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def predict(self, xyz, radius, sdf):
+        x = np.ascontiguousarray(xyz, np.float64)
+        r = np.ascontiguousarray(np.broadcast_to(radius, (len(x),)), np.float32)
+        s = np.ascontiguousarray(sdf, np.float32)
+        out = np.empty((len(x), 4), np.float32)
+        self._ck(self._L.rbf_mlp_predict(self._h, len(x), _ptr(x), _ptr(r), _ptr(s), _ptr(out)))
+        return out
+
+    def warm_start(self, solver: "Solver", scale: float = 1.0):
+        self._ck(self._L.rbf_mlp_warm_start(self._h, solver._h, float(scale)))
+
+    def launch_count(self) -> int:
+        return int(self._L.rbf_mlp_launch_count(self._h))

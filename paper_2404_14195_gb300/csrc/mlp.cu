@@ -1,0 +1,806 @@
+// mlp.cu — the learned warm start: a Fourier-feature MLP (64 -> 128 x 4 GELU -> 16)
+// trained and evaluated with hand-written BF16 tensor-core (tcgen05) GEMMs, FP32
+// accumulation in tensor memory, fused epilogues, and Adam on FP32 master weights.
+//
+// Every layer is C = A B^T with both operands K-major BF16 (row-major with the
+// reduction index contiguous):
+//   forward   Z_l = H_{l-1} W_l^T           (A = activations [B][in], B = W_l [out][in])
+//   backward  dH_{l-1} = dZ_l W_l           (A = dZ_l [B][out],  B = W_l^T [in][out])
+//             dW_l = dZ_l^T H_{l-1}         (A = dZ_l^T [out][B], B = H_{l-1}^T [in][B]),
+//             split over the batch, partials reduced in FP32
+// so the epilogues also write the transposed copies the weight-gradient GEMMs
+// read, and the optimizer writes W and W^T in BF16.  The network is not in the
+// paper; it implements the build's warm-start design (features of position,
+// radius and wall distance -> (u, v, w, p)).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "acm.cuh"
+#include "ctx.cuh"
+#include "rbfgb.h"
+#include "tc.cuh"
+
+using namespace rbf;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int N_IN = 64, N_H = 128, N_OUT = 4, N_OUT_PAD = 16, N_LAYERS = 5;
+__host__ __device__ constexpr int fan_in(int l) { return l == 0 ? N_IN : N_H; }
+__host__ __device__ constexpr int fan_out(int l) { return l == N_LAYERS - 1 ? N_OUT_PAD : N_H; }
+
+int64_t w_off(int l) {  // offset of W_l in the packed parameter vector
+    int64_t o = 0;
+    for (int i = 0; i < l; ++i) o += (int64_t)fan_out(i) * fan_in(i) + fan_out(i);
+    return o;
+}
+int64_t b_off(int l) { return w_off(l) + (int64_t)fan_out(l) * fan_in(l); }
+int64_t n_params_total() { return w_off(N_LAYERS); }
+
+// ---- tcgen05 GEMM -------------------------------------------------------------------
+enum { EP_F32 = 0, EP_FWD = 1, EP_OUT = 2, EP_BWD = 3, EP_PRED = 4 };
+
+struct GemmArgs {
+    const bf16 *A;
+    int lda;
+    const bf16 *B;
+    int ldb;
+    int M, N, K;          // M multiple of 128; N in {16, 32, 64, 128}; K multiple of 16, split by gridDim.y
+    // epilogue operands
+    float *out32;         // EP_F32: partials [split][M][N]; EP_PRED: [M][4]
+    const float *bias;    // N
+    bf16 *H, *Ht, *G;     // EP_FWD / EP_OUT / EP_BWD outputs (row-major [M][N], transposed [N][ldt], G [M][N])
+    int ldt;
+    const float *T;       // EP_OUT targets [M][4]
+    float *loss, *db;     // accumulators
+    const bf16 *Gin;      // EP_BWD: GELU'(Z) of the layer below, [M][N]
+    int nvalid;
+    float gscale;
+    int32_t *err;
+};
+
+constexpr int SMEM_A = 16384, SMEM_B = 16384;
+constexpr size_t GEMM_SMEM = 57344;  // also caps residency at 3-4 CTAs per SM (<= 512 TMEM columns)
+constexpr uint64_t WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ float gelu_f(float z) {
+    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
+    return 0.5f * z * (1.0f + t);
+}
+__device__ __forceinline__ float gelu_prime_f(float z) {
+    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
+}
+
+// copy rows [r0, r0 + nrows) x cols [k0, k0 + kw) of a K-major BF16 matrix into the
+// no-swizzle core-matrix layout: element (r, k) at (r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2
+__device__ __forceinline__ void stage_tile(uint8_t *dst, const bf16 *src, int ld, int r0, int nrows, int k0, int kw) {
+    const int kp_n = kw >> 3;
+    for (int p = threadIdx.x; p < nrows * kp_n; p += blockDim.x) {
+        const int r = p / kp_n, kp = p - r * kp_n;
+        const uint4 v = *reinterpret_cast<const uint4 *>(src + (int64_t)(r0 + r) * ld + k0 + kp * 8);
+        *reinterpret_cast<uint4 *>(dst + (r >> 3) * 1024 + kp * 128 + (r & 7) * 16) = v;
+    }
+}
+
+template <int EP>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + SMEM_A;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + SMEM_A + SMEM_B);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + SMEM_A + SMEM_B + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128;
+    const int kid = blockIdx.y, ksplit = gridDim.y;
+    const int Kper = g.K / ksplit, k_lo = kid * Kper;
+    const int N = g.N;
+    const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+    if (warp == 0) {
+        tc::tmem_alloc(slot, ncols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(bar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int kc = 0; kc < Kper && ok; kc += 64) {
+        const int kw = min(64, Kper - kc);
+        stage_tile(sA, g.A, g.lda, m0, 128, k_lo + kc, kw);
+        stage_tile(sB, g.B, g.ldb, 0, N, k_lo + kc, kw);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int kk = 0; kk < (kw >> 4); ++kk) {
+                const uint64_t da = tc::smem_desc(sA + kk * 256, 128, 1024);
+                const uint64_t db = tc::smem_desc(sB + kk * 256, 128, 1024);
+                tc::mma_bf16(tmem, da, db, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(bar);
+        }
+        ok = tc::mbar_wait(bar, phase, WAIT_NS);
+        phase ^= 1;
+        __syncthreads();
+    }
+    if (!ok) {  // the MMAs did not complete in time: report, give them one more bounded wait, free TMEM
+        if (tid == 0) atomicExch(g.err, 1);
+        tc::mbar_wait(bar, phase ^ 1, WAIT_NS);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+        return;
+    }
+    tc::fence_after_sync();
+    const int m = m0 + warp * 32 + lane;
+    const bool valid = m < g.nvalid;
+    float lsum = 0.0f;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (EP == EP_F32) {
+            float *o = g.out32 + ((int64_t)kid * g.M + m) * N + c0;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else if (EP == EP_PRED) {
+            if (c0 == 0 && valid)
+#pragma unroll
+                for (int i = 0; i < N_OUT; ++i) g.out32[(int64_t)m * N_OUT + i] = v[i] + g.bias[i];
+        } else {
+            __align__(16) bf16 hv[16];
+            __align__(16) bf16 gv[16];
+            float colv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = c0 + i;
+                float h, gp = 0.0f;
+                if (EP == EP_FWD) {
+                    const float z = v[i] + g.bias[c];
+                    h = gelu_f(z);
+                    gp = gelu_prime_f(z);
+                } else if (EP == EP_OUT) {
+                    const float y = v[i] + g.bias[c];
+                    float dy = 0.0f;
+                    if (c < N_OUT && valid) {
+                        const float e = y - g.T[(int64_t)m * N_OUT + c];
+                        lsum += e * e;
+                        dy = g.gscale * e;
+                    }
+                    h = dy;
+                } else {  // EP_BWD
+                    h = valid ? v[i] * __bfloat162float(g.Gin[(int64_t)m * N + c]) : 0.0f;
+                }
+                hv[i] = __float2bfloat16(h);
+                gv[i] = __float2bfloat16(gp);
+                colv[i] = __bfloat162float(hv[i]);
+            }
+            if (g.H) {
+                uint4 *dst = reinterpret_cast<uint4 *>(g.H + (int64_t)m * N + c0);
+                dst[0] = reinterpret_cast<uint4 *>(hv)[0];
+                dst[1] = reinterpret_cast<uint4 *>(hv)[1];
+            }
+            if (g.G) {
+                uint4 *dst = reinterpret_cast<uint4 *>(g.G + (int64_t)m * N + c0);
+                dst[0] = reinterpret_cast<uint4 *>(gv)[0];
+                dst[1] = reinterpret_cast<uint4 *>(gv)[1];
+            }
+            if (g.Ht)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) g.Ht[(int64_t)(c0 + i) * g.ldt + m] = hv[i];
+            if (g.db && (EP == EP_OUT || EP == EP_BWD)) {  // bias gradient: column sums over the tile's rows
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float s = colv[i];
+                    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                    if (lane == 0 && s != 0.0f) atomicAdd(g.db + c0 + i, s);
+                }
+            }
+        }
+    }
+    if (EP == EP_OUT && g.loss) {
+        for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+        if (lane == 0) atomicAdd(g.loss, lsum);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+cudaError_t launch_gemm(int ep, const GemmArgs &g, int ksplit, cudaStream_t st) {
+    if (g.M % 128 || g.K % 16 || (g.K / ksplit) % 16 || g.K % ksplit || !(g.N == 16 || g.N == 32 || g.N == 64 || g.N == 128))
+        return cudaErrorInvalidValue;
+    dim3 grid(g.M / 128, ksplit);
+    switch (ep) {
+    case EP_F32: k_gemm<EP_F32><<<grid, 128, GEMM_SMEM, st>>>(g); break;
+    case EP_FWD: k_gemm<EP_FWD><<<grid, 128, GEMM_SMEM, st>>>(g); break;
+    case EP_OUT: k_gemm<EP_OUT><<<grid, 128, GEMM_SMEM, st>>>(g); break;
+    case EP_BWD: k_gemm<EP_BWD><<<grid, 128, GEMM_SMEM, st>>>(g); break;
+    case EP_PRED: k_gemm<EP_PRED><<<grid, 128, GEMM_SMEM, st>>>(g); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_set_smem() {
+    cudaError_t e = cudaSuccess;
+    for (auto f : {k_gemm<EP_F32>, k_gemm<EP_FWD>, k_gemm<EP_OUT>, k_gemm<EP_BWD>, k_gemm<EP_PRED>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+// ---- features, targets, reductions, optimizer ------------------------------------------
+__constant__ int c_waves[16][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},   {1, -1, 0}, {1, 0, 1},
+                                   {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},   {1, 1, -1}, {1, -1, 1},
+                                   {1, -1, -1}, {2, 0, 0}, {0, 2, 0},  {0, 0, 2}};
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Rows b < B of X [B][64] and X^T [64][ldt]: sample s = explicit index, or the
+// counter-based draw splitmix64(seed * 2^32 + step * B + b) mod n (step read from
+// *step_dev so a captured graph draws a new batch each replay); targets into T.
+__global__ void k_features(int B, int64_t n, const double *__restrict__ xyz, const float *__restrict__ rad,
+                           const float *__restrict__ sdf, const float *__restrict__ tgt, const int64_t *__restrict__ idx,
+                           uint64_t seed, const int64_t *step_dev, bf16 *X, bf16 *Xt, int ldt, float *T) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    int64_t s;
+    if (idx) s = idx[b];
+    else {
+        const uint64_t c = seed * (1ull << 32) + (uint64_t)(*step_dev) * (uint64_t)B + (uint64_t)b;
+        s = (int64_t)(splitmix64(c) % (uint64_t)n);
+    }
+    const double x = xyz[3 * s], y = xyz[3 * s + 1], z = xyz[3 * s + 2];
+    __align__(16) bf16 row[N_IN];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        double sn, cs;
+        sincospi(2.0 * (c_waves[j][0] * x + c_waves[j][1] * y + c_waves[j][2] * z), &sn, &cs);
+        row[2 * j] = __double2bfloat16(sn);
+        row[2 * j + 1] = __double2bfloat16(cs);
+    }
+    row[32] = __float2bfloat16(rad[s]);
+    row[33] = __float2bfloat16(sdf[s]);
+#pragma unroll
+    for (int j = 34; j < N_IN; ++j) row[j] = __float2bfloat16(0.0f);
+    uint4 *dst = reinterpret_cast<uint4 *>(X + (int64_t)b * N_IN);
+#pragma unroll
+    for (int j = 0; j < N_IN / 8; ++j) dst[j] = reinterpret_cast<uint4 *>(row)[j];
+    if (Xt)
+#pragma unroll
+        for (int j = 0; j < N_IN; ++j) Xt[(int64_t)j * ldt + b] = row[j];
+    if (T && tgt)
+#pragma unroll
+        for (int c = 0; c < N_OUT; ++c) T[(int64_t)b * N_OUT + c] = tgt[s * N_OUT + c];
+}
+
+// out[m][n] (or out[n][m] when transposed) = sum over splits of part[k][m][n]
+__global__ void k_reduce_splits(const float *__restrict__ part, int ksplit, int M, int N, float *out, int transposed) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * N) return;
+    float s = 0.0f;
+    for (int k = 0; k < ksplit; ++k) s += part[(int64_t)k * M * N + t];
+    const int m = t / N, n = t - m * N;
+    out[transposed ? n * M + m : t] = s;
+}
+
+// Adam on the packed FP32 parameters, then the BF16 copies W_l [out][in] and W_l^T [in][out]
+struct BfPtrs {
+    bf16 *W[N_LAYERS], *Wt[N_LAYERS];
+};
+__global__ void k_adam(int64_t np, float *theta, const float *grad, float *m, float *v, const int64_t *t_dev, float lr,
+                       float b1, float b2, float eps, int update, BfPtrs bp) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float th = theta[p];
+    if (update) {
+        const int64_t t = *t_dev + 1;
+        const float gp = grad[p];
+        const float mm = b1 * m[p] + (1.0f - b1) * gp;
+        const float vv = b2 * v[p] + (1.0f - b2) * gp * gp;
+        m[p] = mm;
+        v[p] = vv;
+        const float mh = mm / (1.0f - powf(b1, (float)t));
+        const float vh = vv / (1.0f - powf(b2, (float)t));
+        th -= lr * mh / (sqrtf(vh) + eps);
+        theta[p] = th;
+    }
+    int64_t o = 0;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const int64_t nw = (int64_t)fan_out(l) * fan_in(l);
+        if (p < o + nw) {
+            const int64_t q = p - o;
+            const int r = (int)(q / fan_in(l)), c = (int)(q - (int64_t)r * fan_in(l));
+            const bf16 hb = __float2bfloat16(th);
+            bp.W[l][q] = hb;
+            bp.Wt[l][(int64_t)c * fan_out(l) + r] = hb;
+            return;
+        }
+        o += nw + fan_out(l);
+        if (p < o) return;  // a bias
+    }
+}
+__global__ void k_incr(int64_t *a, int64_t *b) {
+    ++*a;
+    if (b) ++*b;
+}
+
+// warm start: predicted (u, v, w, p) into ACM fields of type T (sorted node order),
+// zero velocity on wall nodes
+template <typename T>
+__global__ void k_inject(int64_t n, const float *__restrict__ pred, const uint8_t *__restrict__ type, float scale,
+                         T *u, T *v, T *w, T *p) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool wall = type[i] != 0;
+    u[i] = wall ? (T)0 : (T)(scale * pred[4 * i]);
+    v[i] = wall ? (T)0 : (T)(scale * pred[4 * i + 1]);
+    w[i] = wall ? (T)0 : (T)(scale * pred[4 * i + 2]);
+    p[i] = (T)(scale * pred[4 * i + 3]);
+}
+// radius and signed wall distance of the context's nodes (sorted order)
+__global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx, double cy, double cz, double r,
+                           float *rad, float *sdf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dx = mimg(xyz[3 * i] - cx), dy = mimg(xyz[3 * i + 1] - cy), dz = mimg(xyz[3 * i + 2] - cz);
+    rad[i] = (float)r;
+    sdf[i] = (float)(sqrt(dx * dx + dy * dy + dz * dz) - r);
+}
+
+}  // namespace
+
+// =====================================================================================
+struct rbf_mlp {
+    template <typename T> using DevArr = rbf::DevArr<T>;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int64_t launches = 0;
+    DevArr<float> theta, m, v, grad;
+    DevArr<bf16> W[N_LAYERS], Wt[N_LAYERS];
+    DevArr<int64_t> counters;  // [0] Adam step t, [1] batch draw step
+    // training data
+    int64_t nd = 0;
+    DevArr<double> dxyz;
+    DevArr<float> drad, dsdf, dtgt;
+    // workspace for batch B
+    int B = 0;
+    DevArr<bf16> X, Xt, H[4], Ht[4], G[4], dY, dYt, dZ[4], dZt[4];
+    DevArr<float> T, part, loss, pred;
+    DevArr<int64_t> idx;
+    DevArr<int32_t> errflag;
+    cudaGraphExec_t gexec = nullptr;
+    int gB = -1;
+    uint64_t gseed = 0;
+    float glr = 0.f;
+};
+
+namespace {
+
+int mfail(rbf_mlp *m, int code, const std::string &msg) {
+    if (m) m->err = msg;
+    return code;
+}
+#define MCK(call)                                                                                         \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return mfail(mm, e_ == cudaErrorMemoryAllocation ? RBF_ENOMEM : RBF_ECUDA,                    \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    } while (0)
+
+struct MDevGuard {
+    int prev = -1;
+    explicit MDevGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~MDevGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+BfPtrs bf_ptrs(rbf_mlp *mm) {
+    BfPtrs b;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        b.W[l] = mm->W[l].p;
+        b.Wt[l] = mm->Wt[l].p;
+    }
+    return b;
+}
+
+int ensure_workspace(rbf_mlp *mm, int B) {
+    if (mm->B == B) return RBF_OK;
+    if (mm->gexec) {
+        cudaGraphExecDestroy(mm->gexec);
+        mm->gexec = nullptr;
+    }
+    MCK(mm->X.alloc((size_t)B * N_IN));
+    MCK(mm->Xt.alloc((size_t)B * N_IN));
+    for (int l = 0; l < 4; ++l) {
+        MCK(mm->H[l].alloc((size_t)B * N_H));
+        MCK(mm->Ht[l].alloc((size_t)B * N_H));
+        MCK(mm->G[l].alloc((size_t)B * N_H));
+        MCK(mm->dZ[l].alloc((size_t)B * N_H));
+        MCK(mm->dZt[l].alloc((size_t)B * N_H));
+    }
+    MCK(mm->dY.alloc((size_t)B * N_OUT_PAD));
+    MCK(mm->dYt.alloc((size_t)B * N_OUT_PAD));
+    MCK(mm->T.alloc((size_t)B * N_OUT));
+    MCK(mm->pred.alloc((size_t)B * N_OUT));
+    MCK(mm->idx.alloc((size_t)B));
+    MCK(mm->part.alloc((size_t)(B / 128) * N_H * N_H));
+    mm->B = B;
+    return RBF_OK;
+}
+
+GemmArgs gemm_args(const bf16 *A, int lda, const bf16 *Bm, int ldb, int M, int N, int K, int32_t *err) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb; g.M = M; g.N = N; g.K = K; g.err = err; g.nvalid = M;
+    return g;
+}
+
+// forward of the B rows in X; train: keep activations, transposes and GELU' and
+// the loss gradient (targets T); otherwise write predictions to pred
+cudaError_t enqueue_forward(rbf_mlp *mm, int B, int nvalid, bool train) {
+    cudaError_t e;
+    const bf16 *in = mm->X.p;
+    int fin = N_IN;
+    for (int l = 0; l < 4; ++l) {
+        GemmArgs g = gemm_args(in, fin, mm->W[l].p, fan_in(l), B, N_H, fin, mm->errflag.p);
+        g.bias = mm->theta.p + b_off(l);
+        g.H = mm->H[l].p;
+        g.Ht = train ? mm->Ht[l].p : nullptr;
+        g.G = train ? mm->G[l].p : nullptr;
+        g.ldt = B;
+        g.nvalid = nvalid;
+        if ((e = launch_gemm(EP_FWD, g, 1, mm->st)) != cudaSuccess) return e;
+        ++mm->launches;
+        in = mm->H[l].p;
+        fin = N_H;
+    }
+    GemmArgs g = gemm_args(in, N_H, mm->W[4].p, N_H, B, N_OUT_PAD, N_H, mm->errflag.p);
+    g.bias = mm->theta.p + b_off(4);
+    g.nvalid = nvalid;
+    if (train) {
+        g.T = mm->T.p;
+        g.H = mm->dY.p;
+        g.Ht = mm->dYt.p;
+        g.ldt = B;
+        g.loss = mm->loss.p;
+        g.db = mm->grad.p + b_off(4);
+        g.gscale = 2.0f / ((float)nvalid * N_OUT);
+        e = launch_gemm(EP_OUT, g, 1, mm->st);
+    } else {
+        g.out32 = mm->pred.p;
+        e = launch_gemm(EP_PRED, g, 1, mm->st);
+    }
+    ++mm->launches;
+    return e;
+}
+
+// backward: gradient of the mean squared error into mm->grad (packed layout)
+cudaError_t enqueue_backward(rbf_mlp *mm, int B) {
+    cudaError_t e;
+    const int ks = B / 128;
+    // dW5^T = H4^T dY  ([128][16], split over the batch)
+    {
+        GemmArgs g = gemm_args(mm->Ht[3].p, B, mm->dYt.p, B, N_H, N_OUT_PAD, B, mm->errflag.p);
+        g.out32 = mm->part.p;
+        if ((e = launch_gemm(EP_F32, g, ks, mm->st)) != cudaSuccess) return e;
+        k_reduce_splits<<<(N_H * N_OUT_PAD + 255) / 256, 256, 0, mm->st>>>(mm->part.p, ks, N_H, N_OUT_PAD,
+                                                                         mm->grad.p + w_off(4), 1);
+        mm->launches += 2;
+    }
+    // dZ4 = (dY W5) * GELU'(Z4)
+    {
+        GemmArgs g = gemm_args(mm->dY.p, N_OUT_PAD, mm->Wt[4].p, N_OUT_PAD, B, N_H, N_OUT_PAD, mm->errflag.p);
+        g.Gin = mm->G[3].p;
+        g.H = mm->dZ[3].p;
+        g.Ht = mm->dZt[3].p;
+        g.ldt = B;
+        g.db = mm->grad.p + b_off(3);
+        if ((e = launch_gemm(EP_BWD, g, 1, mm->st)) != cudaSuccess) return e;
+        ++mm->launches;
+    }
+    for (int l = 3; l >= 0; --l) {
+        // dW_l = dZ_l^T H_{l-1}
+        const bf16 *Hin_t = l > 0 ? mm->Ht[l - 1].p : mm->Xt.p;
+        const int fin = fan_in(l);
+        GemmArgs g = gemm_args(mm->dZt[l].p, B, Hin_t, B, N_H, fin, B, mm->errflag.p);
+        g.out32 = mm->part.p;
+        if ((e = launch_gemm(EP_F32, g, ks, mm->st)) != cudaSuccess) return e;
+        k_reduce_splits<<<(N_H * fin + 255) / 256, 256, 0, mm->st>>>(mm->part.p, ks, N_H, fin, mm->grad.p + w_off(l), 0);
+        mm->launches += 2;
+        if (l == 0) break;
+        // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
+        GemmArgs h = gemm_args(mm->dZ[l].p, N_H, mm->Wt[l].p, N_H, B, N_H, N_H, mm->errflag.p);
+        h.Gin = mm->G[l - 1].p;
+        h.H = mm->dZ[l - 1].p;
+        h.Ht = mm->dZt[l - 1].p;
+        h.ldt = B;
+        h.db = mm->grad.p + b_off(l - 1);
+        if ((e = launch_gemm(EP_BWD, h, 1, mm->st)) != cudaSuccess) return e;
+        ++mm->launches;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_train_step(rbf_mlp *mm, int B, uint64_t seed, float lr, const int64_t *explicit_idx, bool update) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(mm->grad.p, 0, mm->grad.n * sizeof(float), mm->st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(mm->loss.p, 0, sizeof(float), mm->st)) != cudaSuccess) return e;
+    k_features<<<(B + 127) / 128, 128, 0, mm->st>>>(B, mm->nd, mm->dxyz.p, mm->drad.p, mm->dsdf.p, mm->dtgt.p,
+                                                    explicit_idx, seed, mm->counters.p + 1, mm->X.p, mm->Xt.p, B, mm->T.p);
+    ++mm->launches;
+    if ((e = enqueue_forward(mm, B, B, true)) != cudaSuccess) return e;
+    if ((e = enqueue_backward(mm, B)) != cudaSuccess) return e;
+    if (update) {
+        const int64_t np = n_params_total();
+        k_adam<<<(unsigned)((np + 255) / 256), 256, 0, mm->st>>>(np, mm->theta.p, mm->grad.p, mm->m.p, mm->v.p,
+                                                                 mm->counters.p, lr, 0.9f, 0.999f, 1e-8f, 1, bf_ptrs(mm));
+        k_incr<<<1, 1, 0, mm->st>>>(mm->counters.p, mm->counters.p + 1);
+        mm->launches += 2;
+    }
+    return cudaGetLastError();
+}
+
+int check_err(rbf_mlp *mm) {
+    int32_t f = 0;
+    MCK(cudaMemcpyAsync(&f, mm->errflag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, mm->st));
+    MCK(cudaStreamSynchronize(mm->st));
+    if (f) return mfail(mm, RBF_ETIMEOUT, "tensor-core wait exceeded its limit");
+    return RBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t rbf_mlp_num_params(void) { return n_params_total(); }
+
+int rbf_mlp_create(rbf_mlp **out, int device, void *stream) {
+    if (!out) return RBF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RBF_ECUDA;
+    rbf_mlp *mm = new rbf_mlp();
+    mm->device = device;
+    MDevGuard dg(device);
+    if (stream) mm->st = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&mm->st, cudaStreamNonBlocking) != cudaSuccess) { delete mm; return RBF_ECUDA; }
+        mm->own_stream = true;
+    }
+    const int64_t np = n_params_total();
+    bool ok = mm->theta.alloc(np) == cudaSuccess && mm->m.alloc(np) == cudaSuccess && mm->v.alloc(np) == cudaSuccess &&
+              mm->grad.alloc(np) == cudaSuccess && mm->counters.alloc(2) == cudaSuccess &&
+              mm->loss.alloc(1) == cudaSuccess && mm->errflag.alloc(1) == cudaSuccess && gemm_set_smem() == cudaSuccess;
+    for (int l = 0; l < N_LAYERS && ok; ++l)
+        ok = mm->W[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess &&
+             mm->Wt[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess;
+    if (!ok) { rbf_mlp_destroy(mm); return RBF_ECUDA; }
+    cudaMemsetAsync(mm->theta.p, 0, np * sizeof(float), mm->st);
+    cudaMemsetAsync(mm->m.p, 0, np * sizeof(float), mm->st);
+    cudaMemsetAsync(mm->v.p, 0, np * sizeof(float), mm->st);
+    cudaMemsetAsync(mm->counters.p, 0, 2 * sizeof(int64_t), mm->st);
+    cudaMemsetAsync(mm->errflag.p, 0, sizeof(int32_t), mm->st);
+    if (cudaStreamSynchronize(mm->st) != cudaSuccess) { rbf_mlp_destroy(mm); return RBF_ECUDA; }
+    *out = mm;
+    return RBF_OK;
+}
+
+int rbf_mlp_destroy(rbf_mlp *mm) {
+    if (!mm) return RBF_EINVAL;
+    {
+        MDevGuard dg(mm->device);
+        if (mm->st) cudaStreamSynchronize(mm->st);
+        if (mm->gexec) cudaGraphExecDestroy(mm->gexec);
+        if (mm->own_stream && mm->st) cudaStreamDestroy(mm->st);
+        delete mm;
+    }
+    return RBF_OK;
+}
+
+const char *rbf_mlp_last_error(const rbf_mlp *mm) { return mm ? mm->err.c_str() : "null"; }
+
+int rbf_mlp_set_params(rbf_mlp *mm, const float *theta) {
+    if (!mm || !theta) return RBF_EINVAL;
+    MDevGuard dg(mm->device);
+    const int64_t np = n_params_total();
+    MCK(cudaMemcpyAsync(mm->theta.p, theta, np * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemsetAsync(mm->m.p, 0, np * sizeof(float), mm->st));
+    MCK(cudaMemsetAsync(mm->v.p, 0, np * sizeof(float), mm->st));
+    MCK(cudaMemsetAsync(mm->counters.p, 0, 2 * sizeof(int64_t), mm->st));
+    k_adam<<<(unsigned)((np + 255) / 256), 256, 0, mm->st>>>(np, mm->theta.p, nullptr, nullptr, nullptr, mm->counters.p,
+                                                             0.f, 0.f, 0.f, 0.f, 0, bf_ptrs(mm));
+    ++mm->launches;
+    MCK(cudaGetLastError());
+    MCK(cudaStreamSynchronize(mm->st));
+    return RBF_OK;
+}
+
+int rbf_mlp_get_params(rbf_mlp *mm, float *theta) {
+    if (!mm || !theta) return RBF_EINVAL;
+    MDevGuard dg(mm->device);
+    MCK(cudaMemcpyAsync(theta, mm->theta.p, n_params_total() * sizeof(float), cudaMemcpyDeviceToHost, mm->st));
+    MCK(cudaStreamSynchronize(mm->st));
+    return RBF_OK;
+}
+
+int rbf_mlp_set_data(rbf_mlp *mm, int64_t n, const double *xyz, const float *radius, const float *sdf,
+                     const float *target) {
+    if (!mm || n < 1 || !xyz || !radius || !sdf || !target) return RBF_EINVAL;
+    MDevGuard dg(mm->device);
+    MCK(mm->dxyz.alloc(3 * n)); MCK(mm->drad.alloc(n)); MCK(mm->dsdf.alloc(n)); MCK(mm->dtgt.alloc(4 * n));
+    MCK(cudaMemcpyAsync(mm->dxyz.p, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemcpyAsync(mm->drad.p, radius, n * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemcpyAsync(mm->dsdf.p, sdf, n * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemcpyAsync(mm->dtgt.p, target, 4 * n * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaStreamSynchronize(mm->st));
+    mm->nd = n;
+    return RBF_OK;
+}
+
+int rbf_mlp_gradient(rbf_mlp *mm, int batch, const int64_t *sample_idx, float *grad, double *loss) {
+    if (!mm || !sample_idx || !grad) return RBF_EINVAL;
+    if (batch < 128 || batch % 128 || batch > (1 << 22)) return mfail(mm, RBF_EINVAL, "batch must be a multiple of 128");
+    if (!mm->nd) return mfail(mm, RBF_EINVAL, "rbf_mlp_gradient: set data first");
+    for (int b = 0; b < batch; ++b)
+        if (sample_idx[b] < 0 || sample_idx[b] >= mm->nd) return mfail(mm, RBF_EINVAL, "sample index out of range");
+    MDevGuard dg(mm->device);
+    int rc = ensure_workspace(mm, batch);
+    if (rc) return rc;
+    MCK(cudaMemcpyAsync(mm->idx.p, sample_idx, batch * sizeof(int64_t), cudaMemcpyHostToDevice, mm->st));
+    MCK(enqueue_train_step(mm, batch, 0, 0.f, mm->idx.p, false));
+    rc = check_err(mm);
+    if (rc) return rc;
+    float l = 0.f;
+    MCK(cudaMemcpyAsync(grad, mm->grad.p, n_params_total() * sizeof(float), cudaMemcpyDeviceToHost, mm->st));
+    MCK(cudaMemcpyAsync(&l, mm->loss.p, sizeof(float), cudaMemcpyDeviceToHost, mm->st));
+    MCK(cudaStreamSynchronize(mm->st));
+    if (loss) *loss = (double)l / ((double)batch * N_OUT);
+    return RBF_OK;
+}
+
+int rbf_mlp_train(rbf_mlp *mm, int steps, int batch, double lr, uint64_t seed, float *loss_hist) {
+    if (!mm || steps < 0) return RBF_EINVAL;
+    if (batch < 128 || batch % 128 || batch > (1 << 22)) return mfail(mm, RBF_EINVAL, "batch must be a multiple of 128");
+    if (!mm->nd) return mfail(mm, RBF_EINVAL, "rbf_mlp_train: set data first");
+    MDevGuard dg(mm->device);
+    int rc = ensure_workspace(mm, batch);
+    if (rc) return rc;
+    if (!mm->gexec || mm->gB != batch || mm->gseed != seed || mm->glr != (float)lr) {
+        if (mm->gexec) cudaGraphExecDestroy(mm->gexec);
+        mm->gexec = nullptr;
+        cudaGraph_t g;
+        MCK(cudaStreamBeginCapture(mm->st, cudaStreamCaptureModeThreadLocal));
+        int64_t l0 = mm->launches;
+        cudaError_t e = enqueue_train_step(mm, batch, seed, (float)lr, nullptr, true);
+        cudaError_t e2 = cudaStreamEndCapture(mm->st, &g);
+        mm->launches = l0;
+        MCK(e);
+        MCK(e2);
+        e = cudaGraphInstantiate(&mm->gexec, g, 0);
+        cudaGraphDestroy(g);
+        MCK(e);
+        mm->gB = batch;
+        mm->gseed = seed;
+        mm->glr = (float)lr;
+    }
+    for (int s = 0; s < steps; ++s) {
+        MCK(cudaGraphLaunch(mm->gexec, mm->st));
+        mm->launches += 4 + 5 + 14 + 2;
+        if (loss_hist) MCK(cudaMemcpyAsync(loss_hist + s, mm->loss.p, sizeof(float), cudaMemcpyDeviceToHost, mm->st));
+    }
+    rc = check_err(mm);
+    if (rc) return rc;
+    if (loss_hist)
+        for (int s = 0; s < steps; ++s) loss_hist[s] /= (float)batch * N_OUT;
+    return RBF_OK;
+}
+
+int rbf_mlp_predict(rbf_mlp *mm, int64_t n, const double *xyz, const float *radius, const float *sdf, float *out) {
+    if (!mm || n < 1 || !xyz || !radius || !sdf || !out) return RBF_EINVAL;
+    MDevGuard dg(mm->device);
+    const int B = 16384;
+    int rc = ensure_workspace(mm, std::max(mm->B, B));
+    if (rc) return rc;
+    const int Bw = mm->B;
+    DevArr<double> px;
+    DevArr<float> pr, ps;
+    MCK(px.alloc(3 * n)); MCK(pr.alloc(n)); MCK(ps.alloc(n));
+    MCK(cudaMemcpyAsync(px.p, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemcpyAsync(pr.p, radius, n * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    MCK(cudaMemcpyAsync(ps.p, sdf, n * sizeof(float), cudaMemcpyHostToDevice, mm->st));
+    std::vector<int64_t> ids(Bw);
+    for (int64_t s0 = 0; s0 < n; s0 += Bw) {
+        const int cnt = (int)std::min<int64_t>(Bw, n - s0);
+        for (int b = 0; b < Bw; ++b) ids[b] = b < cnt ? s0 + b : s0;
+        MCK(cudaMemcpyAsync(mm->idx.p, ids.data(), Bw * sizeof(int64_t), cudaMemcpyHostToDevice, mm->st));
+        k_features<<<(Bw + 127) / 128, 128, 0, mm->st>>>(Bw, n, px.p, pr.p, ps.p, nullptr, mm->idx.p, 0, mm->counters.p + 1,
+                                                        mm->X.p, nullptr, Bw, nullptr);
+        ++mm->launches;
+        MCK(enqueue_forward(mm, Bw, cnt, false));
+        MCK(cudaMemcpyAsync(out + 4 * s0, mm->pred.p, (size_t)cnt * 4 * sizeof(float), cudaMemcpyDeviceToHost, mm->st));
+        MCK(cudaStreamSynchronize(mm->st));  // ids is reused
+    }
+    return check_err(mm);
+}
+
+int rbf_mlp_warm_start(rbf_mlp *mm, rbf_ctx *ctx, double scale) {
+    if (!mm || !ctx) return RBF_EINVAL;
+    if (!ctx->inited || ctx->solver != RBF_SOLVER_ACM) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: needs an initialised ACM context");
+    if (!ctx->has_sphere) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: the context has no sphere");
+    if (ctx->device != mm->device) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: different devices");
+    MDevGuard dg(mm->device);
+    const int64_t n = ctx->n;
+    // order the context's stream after the network's
+    MCK(cudaStreamSynchronize(ctx->st));
+    int rc = ensure_workspace(mm, std::max(mm->B, 16384));
+    if (rc) return rc;
+    const int Bw = mm->B;
+    DevArr<float> rad, sdf, predall;
+    MCK(rad.alloc(n)); MCK(sdf.alloc(n)); MCK(predall.alloc(4 * n));
+    k_node_geo<<<(unsigned)((n + 255) / 256), 256, 0, mm->st>>>(n, ctx->xyz.p, ctx->c[0], ctx->c[1], ctx->c[2], ctx->r, rad.p, sdf.p);
+    ++mm->launches;
+    std::vector<int64_t> ids(Bw);
+    for (int64_t s0 = 0; s0 < n; s0 += Bw) {
+        const int cnt = (int)std::min<int64_t>(Bw, n - s0);
+        for (int b = 0; b < Bw; ++b) ids[b] = b < cnt ? s0 + b : s0;
+        MCK(cudaMemcpyAsync(mm->idx.p, ids.data(), Bw * sizeof(int64_t), cudaMemcpyHostToDevice, mm->st));
+        k_features<<<(Bw + 127) / 128, 128, 0, mm->st>>>(Bw, n, ctx->xyz.p, rad.p, sdf.p, nullptr, mm->idx.p, 0,
+                                                        mm->counters.p + 1, mm->X.p, nullptr, Bw, nullptr);
+        ++mm->launches;
+        MCK(enqueue_forward(mm, Bw, cnt, false));
+        MCK(cudaMemcpyAsync(predall.p + 4 * s0, mm->pred.p, (size_t)cnt * 4 * sizeof(float), cudaMemcpyDeviceToDevice, mm->st));
+        MCK(cudaStreamSynchronize(mm->st));
+    }
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    if (ctx->prec == RBF_FP32)
+        k_inject<float><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, (float)scale, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p);
+    else
+        k_inject<double><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, (float)scale, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p);
+    ++mm->launches;
+    MCK(cudaGetLastError());
+    MCK(cudaStreamSynchronize(mm->st));
+    // C of Eq. MNS_C from the new velocity, in the slot the next pressure sweep reads
+    const int slot = (ctx->parity + 1) & 1;
+    if (ctx->prec == RBF_FP32) {
+        AcmArgs<float> a;
+        std::memset(&a, 0, sizeof(a));
+        a.n = n; a.u = ctx->a32[0].p; a.v = ctx->a32[1].p; a.w_ = ctx->a32[2].p; a.vmax = ctx->vmax.p;
+        MCK(acm_launch_vmax<float>(a, slot, ctx->st));
+    } else {
+        AcmArgs<double> a;
+        std::memset(&a, 0, sizeof(a));
+        a.n = n; a.u = ctx->a64[0].p; a.v = ctx->a64[1].p; a.w_ = ctx->a64[2].p; a.vmax = ctx->vmax.p;
+        MCK(acm_launch_vmax<double>(a, slot, ctx->st));
+    }
+    MCK(cudaStreamSynchronize(ctx->st));
+    return check_err(mm);
+}
+
+int64_t rbf_mlp_launch_count(const rbf_mlp *mm) { return mm ? mm->launches : -1; }
+
+}  // extern "C"
