@@ -176,7 +176,9 @@ typedef struct {
 
 /* Step until the criterion holds or max_steps: returns RBF_OK or
  * RBF_ENOTCONVERGED (res filled in both cases), RBF_EDIVERGED on non-finite
- * fields. */
+ * fields.  ACM runs as one persistent cooperative kernel that checks the residual
+ * on the device every check_every steps (RBF_ETIMEOUT if its grid barrier times
+ * out); LBM steps in CUDA graphs and checks k/d^2 on the host. */
 int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res);
 
 /* Device time of the last rbf_step (milliseconds, CUDA events on the context
@@ -216,6 +218,42 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
+
+/* ---- batched cells ----------------------------------------------------------
+ * Many periodic cells (their own nodes, sphere and stencil size N_L), e.g. a
+ * porosity sweep (the paper's section on various porosities).  The weight systems
+ * of every node of every cell are solved in one launch (and the wall Neumann
+ * systems of every cell in a second one); the ACM steps of all cells run in one
+ * persistent cooperative launch, each cell stopping at its own criterion.
+ * Each cell is an ordinary rbf_ctx (borrow it with rbf_batch_cell to read fields,
+ * permeability or drag; it is owned by the batch). */
+typedef struct rbf_batch rbf_batch;
+typedef struct {
+    int64_t steps;       /* steps this cell took in the last rbf_batch_solve */
+    double residual;     /* its last relative velocity change */
+    double k_over_d2;    /* its permeability (probe grid m_p) */
+    int status;          /* 0 converged, 1 step cap, 2 non-finite */
+} rbf_batch_cell_result;
+int rbf_batch_create(rbf_batch **out, int device, void *cuda_stream);
+int rbf_batch_destroy(rbf_batch *b);
+const char *rbf_batch_last_error(const rbf_batch *b);
+/* Add a cell (arguments as rbf_set_nodes, rbf_set_sphere and rbf_build_stencils);
+ * returns the cell's index (>= 0) or a negative RBF_E* code.  At most 128 cells. */
+int rbf_batch_add_cell(rbf_batch *b, int64_t n, const double *xyz, const uint8_t *type, const double *normal,
+                       const double c[3], double r, int n_l);
+/* Stencils of every cell, then the ACM weights (PHS r^phs_k + monomials of degree
+ * <= mono_m) of all cells in one launch.  rep: totals and the smallest h_min. */
+int rbf_batch_build(rbf_batch *b, int phs_k, int mono_m, rbf_weight_report *rep);
+/* rbf_init on every cell (ACM; each cell gets its own dt from its own h_min). */
+int rbf_batch_init(rbf_batch *b, const rbf_params *p);
+/* Steady solve of all cells in one persistent launch: per-cell stop when the
+ * relative velocity change (checked every opts->check_every steps) is below
+ * opts->tol, or at opts->max_steps.  res: one entry per cell.  Returns RBF_OK
+ * when every cell converged, RBF_ENOTCONVERGED otherwise (res filled),
+ * RBF_ETIMEOUT if a grid barrier of the persistent kernel timed out. */
+int rbf_batch_solve(rbf_batch *b, const rbf_solve_opts *opts, rbf_batch_cell_result *res);
+int rbf_batch_num_cells(const rbf_batch *b);
+rbf_ctx *rbf_batch_cell(rbf_batch *b, int cell);
 
 /* ---- learned warm start ------------------------------------------------------
  * The paper has no network; this is the build's warm start for the steady ACM

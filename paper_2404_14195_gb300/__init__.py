@@ -55,6 +55,11 @@ class rbf_tune_report(ctypes.Structure):
                 ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int)]
 
 
+class rbf_batch_cell_result(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("residual", ctypes.c_double), ("k_over_d2", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
 class rbf_solve_opts(ctypes.Structure):
     _fields_ = [("max_steps", ctypes.c_int64), ("check_every", ctypes.c_int), ("tol", ctypes.c_double),
                 ("m_p", ctypes.c_int)]
@@ -95,6 +100,15 @@ ABI = {
     "rbf_set_kernel_variant": (_I, [_P, _I]),
     "rbf_permeability_static": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rbf_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
+    "rbf_batch_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "rbf_batch_destroy": (_I, [_P]),
+    "rbf_batch_last_error": (ctypes.c_char_p, [_P]),
+    "rbf_batch_add_cell": (_I, [_P, _I64, _P, _P, _P, _P, _D, _I]),
+    "rbf_batch_build": (_I, [_P, _I, _I, ctypes.POINTER(rbf_weight_report)]),
+    "rbf_batch_init": (_I, [_P, ctypes.POINTER(rbf_params)]),
+    "rbf_batch_solve": (_I, [_P, ctypes.POINTER(rbf_solve_opts), _P]),
+    "rbf_batch_num_cells": (_I, [_P]),
+    "rbf_batch_cell": (_P, [_P, _I]),
     "rbf_mlp_num_params": (_I64, []),
     "rbf_mlp_create": (_I, [ctypes.POINTER(_P), _I, _P]),
     "rbf_mlp_destroy": (_I, [_P]),
@@ -302,6 +316,92 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(self._L.rbf_launch_count(self._h))
+
+
+def _params(precision=RBF_FP64, nu=1.0, g=(1.0, 0.0, 0.0), rho=1.0, dt=0.0, cfl=0.1, beta=10.0, v_ref=0.0,
+            n_p=3, tau_plus=0.8, magic=3.0 / 16.0):
+    p = rbf_params()
+    p.precision = precision
+    p.nu = nu
+    p.g[0], p.g[1], p.g[2] = g
+    p.rho, p.dt, p.cfl, p.beta, p.v_ref, p.n_p = rho, dt, cfl, beta, v_ref, n_p
+    p.tau_plus, p.magic = tau_plus, magic
+    return p
+
+
+class _BorrowedSolver(Solver):
+    """A cell of a Batch seen as a Solver (the batch owns the context)."""
+
+    def __init__(self, L, handle, n, n_l):
+        self._L = L
+        self._h = ctypes.c_void_p(handle)
+        self.n, self.n_l, self.q, self.solver = n, n_l, 0, RBF_SOLVER_ACM
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Many cells solved together: one weight launch, one persistent step launch."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        rc = L.rbf_batch_create(ctypes.byref(h), device, stream)
+        if rc != RBF_OK:
+            raise RbfError(rc, "rbf_batch_create failed (no usable CUDA device?)")
+        self._h = h
+        self._cells = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rbf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc, ok=(RBF_OK,)):
+        if rc not in ok:
+            raise RbfError(rc, self._L.rbf_batch_last_error(self._h).decode())
+        return rc
+
+    def add_cell(self, case, n_l: int):
+        x = np.ascontiguousarray(case["xyz"], np.float64)
+        t = np.ascontiguousarray(case["type"], np.uint8)
+        nr = np.ascontiguousarray(case["normal"], np.float64)
+        c = np.ascontiguousarray(case["centre"], np.float64)
+        rc = self._L.rbf_batch_add_cell(self._h, len(x), _ptr(x), _ptr(t), _ptr(nr), _ptr(c), float(case["radius"]), n_l)
+        if rc < 0:
+            self._ck(rc)
+        self._cells.append((len(x), n_l))
+        return rc
+
+    def build(self, k: int = 3, m: int = 2):
+        rep = rbf_weight_report()
+        self._ck(self._L.rbf_batch_build(self._h, k, m, ctypes.byref(rep)))
+        return dict(n_systems=rep.n_systems, n_singular=rep.n_singular, h_min=rep.h_min)
+
+    def init(self, **kw):
+        p = _params(**kw)
+        self._ck(self._L.rbf_batch_init(self._h, ctypes.byref(p)))
+
+    def solve(self, max_steps: int, tol: float, check_every: int = 100, m_p: int = 32):
+        o = rbf_solve_opts(max_steps, check_every, tol, m_p)
+        res = (rbf_batch_cell_result * len(self._cells))()
+        self._ck(self._L.rbf_batch_solve(self._h, ctypes.byref(o), res), ok=(RBF_OK, RBF_ENOTCONVERGED))
+        return [dict(steps=r.steps, residual=r.residual, k_over_d2=r.k_over_d2, status=r.status) for r in res]
+
+    def cell(self, i: int) -> Solver:
+        h = self._L.rbf_batch_cell(self._h, i)
+        if not h:
+            raise RbfError(RBF_EINVAL, "no such cell")
+        n, n_l = self._cells[i]
+        return _BorrowedSolver(self._L, h, n, n_l)
 
 
 class Mlp:

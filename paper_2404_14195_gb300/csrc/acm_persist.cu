@@ -1,0 +1,270 @@
+// acm_persist.cu — the ACM steady driver as one persistent kernel over any number
+// of cells (MNS algorithm of the appendix, repeated until each cell's stopping
+// criterion holds).
+//
+// One cooperative launch; every block loops over steps and, inside a step, over
+// the phases  predict -> n_p x (pressure, wall pressure, correction),  each phase
+// a grid-stride loop over 32-node SELL slices of all cells still running (warp =
+// slice, lane = node), separated by a software grid barrier.  Every check_every
+// steps the blocks reduce, per cell, |v - v_prev|^2 and |v|^2 in FP64, block 0
+// turns them into residuals and sets the cell's done flag; converged cells drop
+// out of the loop while the others continue.  The arithmetic of each phase is
+// that of the multi-launch kernels in acm.cu (same operations, same order).
+//
+// The grid barrier is a counter plus a generation word; waiting blocks give up
+// after a wall-clock limit, raise an error flag and leave the loop, so a launch
+// whose blocks are not co-resident ends with RBF_ETIMEOUT instead of hanging.
+// The cooperative launch itself guarantees co-residency.
+#include "acm_persist.cuh"
+#include "tc.cuh"
+
+namespace rbf {
+
+namespace {
+
+constexpr uint64_t BARRIER_NS = 2000000000ull;
+
+// returns false (and raises *err) if the other blocks did not arrive in time
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int32_t *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = tc::globaltimer_ns();
+            while (*vgen == g) {
+                if (*(volatile int32_t *)err) { ok = 0; break; }
+                if (tc::globaltimer_ns() - t0 > BARRIER_NS) {
+                    atomicExch(err, 2);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ double slot_C(const unsigned long long *slot, double beta, double vref) {
+    const double vmax = __longlong_as_double((long long)*(volatile unsigned long long *)slot);
+    return beta * (vmax > vref ? vmax : vref);
+}
+
+template <typename T>
+__device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool snapshot) {
+    const int64_t i = (ls << 5) + lane;
+    if (i >= c.n) return;
+    const T ui = c.u[i], vi = c.v[i], wi = c.w_[i];
+    if (snapshot) { c.uo[i] = ui; c.vo[i] = vi; c.wo[i] = wi; }
+    if (c.type[i]) { c.us[i] = (T)0; c.vs[i] = (T)0; c.ws[i] = (T)0; return; }
+    const int n_l = c.n_l;
+    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
+    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
+    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+    for (int j = 0; j < n_l; ++j) {
+        const int q = ip[j << 5];
+        const T wx = wp[j << 5], wy = wp[(n_l + j) << 5], wz = wp[(2 * n_l + j) << 5], wl = wp[(3 * n_l + j) << 5];
+        const T uq = c.u[q], vq = c.v[q], wq = c.w_[q];
+        gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
+        gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
+        gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
+    }
+    const T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
+    const T adv_v = ui * gv[0] + vi * gv[1] + wi * gv[2];
+    const T adv_w = ui * gw[0] + vi * gw[1] + wi * gw[2];
+    c.us[i] = ui + c.dt * (c.nu * gu[3] - adv_u + c.gx);
+    c.vs[i] = vi + c.dt * (c.nu * gv[3] - adv_v + c.gy);
+    c.ws[i] = wi + c.dt * (c.nu * gw[3] - adv_w + c.gz);
+}
+
+template <typename T>
+__device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool first, int g) {
+    const int64_t i = (ls << 5) + lane;
+    if (i >= c.n || c.type[i]) return;
+    const T *u = first ? c.us : c.u;
+    const T *v = first ? c.vs : c.v;
+    const T *w = first ? c.ws : c.w_;
+    const double C = slot_C(c.vmax + (g ^ 1), c.beta, c.vref);
+    const int n_l = c.n_l;
+    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
+    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
+    T div = 0;
+    for (int j = 0; j < n_l; ++j) {
+        const int q = ip[j << 5];
+        div += wp[j << 5] * u[q] + wp[(n_l + j) << 5] * v[q] + wp[(2 * n_l + j) << 5] * w[q];
+    }
+    const T Ct = (T)C;
+    c.p[i] = c.p[i] - c.dt * Ct * Ct * c.rho * div;
+}
+
+template <typename T>
+__device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
+    const int64_t b = (ls << 5) + lane;
+    if (b >= c.nb) return;
+    const int n_l = c.n_l;
+    const int32_t *__restrict__ ip = c.idxb + ((ls * n_l) << 5) + lane;
+    const T *__restrict__ wp = c.wn + ((ls * n_l) << 5) + lane;
+    T acc = 0;
+    for (int j = 1; j < n_l; ++j) acc += wp[j << 5] * c.p[ip[j << 5]];
+    c.p[c.wall[b]] = -acc / wp[0];
+}
+
+template <typename T>
+__device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
+    const int64_t i = (ls << 5) + lane;
+    if (i >= c.n) return 0.0;
+    if (c.type[i]) { c.u[i] = (T)0; c.v[i] = (T)0; c.w_[i] = (T)0; return 0.0; }
+    const int n_l = c.n_l;
+    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
+    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
+    T gx = 0, gy = 0, gz = 0;
+    for (int j = 0; j < n_l; ++j) {
+        const T pq = c.p[ip[j << 5]];
+        gx += wp[j << 5] * pq;
+        gy += wp[(n_l + j) << 5] * pq;
+        gz += wp[(2 * n_l + j) << 5] * pq;
+    }
+    const T f = c.dt / c.rho;
+    const T un = c.us[i] - f * gx, vn = c.vs[i] - f * gy, wn = c.ws[i] - f * gz;
+    c.u[i] = un; c.v[i] = vn; c.w_[i] = wn;
+    return (double)sqrt(un * un + vn * vn + wn * wn);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__restrict__ cells, PersistCtl ctl) {
+    __shared__ double racc[PERSIST_MAX_CELLS][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int64_t wstride = (int64_t)gridDim.x * wpb;
+    const int64_t w0 = (int64_t)blockIdx.x * wpb + warp;
+    const unsigned nblocks = gridDim.x;
+    for (int64_t step = 0; step < ctl.max_steps; ++step) {
+        // every block sees the same done flags here (they change only before a barrier)
+        bool any = false;
+        for (int c = 0; c < ctl.ncells; ++c) any |= !((volatile int32_t *)ctl.done)[c];
+        if (!any || *(volatile int32_t *)ctl.err) break;
+        const bool check = ((step + 1) % ctl.check_every == 0) || (step + 1 == ctl.max_steps);
+        for (int64_t s = w0; s < ctl.nslices; s += wstride) {
+            const int2 sl = ctl.slices[s];
+            if (ctl.done[sl.x]) continue;
+            phase_predict<T>(cells[sl.x], sl.y, lane, check);
+        }
+        if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
+        bool broke = false;
+        for (int it = 0; it < ctl.n_p && !broke; ++it) {
+            // slot parity of iteration `it` of this step for each cell: (parity0 + n_p * step + it) & 1
+            if (blockIdx.x == 0 && threadIdx.x < ctl.ncells && !ctl.done[threadIdx.x]) {
+                const CellDesc<T> &c = cells[threadIdx.x];
+                const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
+                c.vmax[g] = 0ULL;
+            }
+            for (int64_t s = w0; s < ctl.nslices; s += wstride) {
+                const int2 sl = ctl.slices[s];
+                if (ctl.done[sl.x]) continue;
+                const CellDesc<T> &c = cells[sl.x];
+                phase_pressure<T>(c, sl.y, lane, it == 0, (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1));
+            }
+            if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
+            for (int64_t s = w0; s < ctl.nwslices; s += wstride) {
+                const int2 sl = ctl.wslices[s];
+                if (ctl.done[sl.x]) continue;
+                phase_wall<T>(cells[sl.x], sl.y, lane);
+            }
+            if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
+            for (int64_t s = w0; s < ctl.nslices; s += wstride) {
+                const int2 sl = ctl.slices[s];
+                if (ctl.done[sl.x]) continue;
+                const CellDesc<T> &c = cells[sl.x];
+                double sp = phase_correct<T>(c, sl.y, lane);
+                for (int off = 16; off > 0; off >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, off));
+                if (lane == 0 && sp > 0.0) {
+                    const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
+                    atomicMax(c.vmax + g, (unsigned long long)__double_as_longlong(sp));
+                }
+            }
+            if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
+        }
+        if (broke) break;
+        if (check) {
+            for (int t = threadIdx.x; t < 2 * ctl.ncells; t += blockDim.x) racc[t >> 1][t & 1] = 0.0;
+            __syncthreads();
+            for (int64_t s = w0; s < ctl.nslices; s += wstride) {
+                const int2 sl = ctl.slices[s];
+                if (ctl.done[sl.x]) continue;
+                const CellDesc<T> &c = cells[sl.x];
+                const int64_t i = ((int64_t)sl.y << 5) + lane;
+                double d2 = 0.0, v2 = 0.0;
+                if (i < c.n && !c.type[i]) {
+                    const double a = (double)c.u[i] - (double)c.uo[i], b = (double)c.v[i] - (double)c.vo[i];
+                    const double e = (double)c.w_[i] - (double)c.wo[i];
+                    d2 = a * a + b * b + e * e;
+                    v2 = (double)c.u[i] * c.u[i] + (double)c.v[i] * c.v[i] + (double)c.w_[i] * c.w_[i];
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+                }
+                if (lane == 0) {
+                    atomicAdd(&racc[sl.x][0], d2);
+                    atomicAdd(&racc[sl.x][1], v2);
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < 2 * ctl.ncells; t += blockDim.x)
+                ctl.partial[(int64_t)blockIdx.x * 2 * PERSIST_MAX_CELLS + t] = racc[t >> 1][t & 1];
+            if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
+            if (blockIdx.x == 0 && threadIdx.x < ctl.ncells) {
+                const int c = threadIdx.x;
+                if (!ctl.done[c]) {
+                    double d2 = 0.0, v2 = 0.0;
+                    for (unsigned b = 0; b < nblocks; ++b) {
+                        d2 += ctl.partial[(int64_t)b * 2 * PERSIST_MAX_CELLS + 2 * c];
+                        v2 += ctl.partial[(int64_t)b * 2 * PERSIST_MAX_CELLS + 2 * c + 1];
+                    }
+                    const double res = v2 > 0.0 ? sqrt(d2) / sqrt(v2) : 0.0;
+                    ctl.resid[c] = res;
+                    ctl.steps[c] = step + 1;
+                    if (!isfinite(res)) { ctl.done[c] = 3; }
+                    else if (v2 > 0.0 && res < ctl.tol) ctl.done[c] = 1;
+                }
+            }
+            if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
+        } else if (blockIdx.x == 0 && threadIdx.x < ctl.ncells && !ctl.done[threadIdx.x]) {
+            ctl.steps[threadIdx.x] = step + 1;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, cudaStream_t st) {
+    void *args[] = {(void *)&cells_dev, (void *)&ctl};
+    return cudaLaunchCooperativeKernel((const void *)k_acm_persistent<T>, dim3(nblocks), dim3(256), args, 0, st);
+}
+
+template <typename T>
+cudaError_t acm_persistent_max_blocks(int *blocks) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T>, 256, 0);
+    *blocks = sms * per;
+    return e;
+}
+
+template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const PersistCtl &, int, cudaStream_t);
+template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, cudaStream_t);
+template cudaError_t acm_persistent_max_blocks<float>(int *);
+template cudaError_t acm_persistent_max_blocks<double>(int *);
+
+}  // namespace rbf

@@ -12,6 +12,7 @@
 
 #include "rbfgb.h"
 #include "acm.cuh"
+#include "acm_persist.cuh"
 #include "ctx.cuh"
 #include "internal.cuh"
 #include "lbm.cuh"
@@ -401,7 +402,13 @@ int rbf_get_stencils(rbf_ctx *ctx, int32_t *idx) {
     return RBF_OK;
 }
 
-int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, double dx, rbf_weight_report *rep) {
+}  // extern "C"
+
+// Weights of one context.  presolved: the node and wall weight systems were already
+// solved into ctx->w64 / ctx->delta / ctx->wgb64 by a multi-cell launch (ACM only),
+// with `ext_sing` singular systems; only the derived arrays and packs remain.
+int compute_weights_impl(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, double dx, rbf_weight_report *rep,
+                         bool presolved, int64_t ext_sing) {
     if (!ctx) return RBF_EINVAL;
     if (!ctx->n_l) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: build stencils first");
     if (phs_k < 3 || phs_k % 2 == 0 || phs_k > 9) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: phs_k must be odd, 3..9");
@@ -432,20 +439,24 @@ int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, 
     CK(d_ops.alloc(ops.size())); CK(d_gops.alloc(3));
     CK(cudaMemcpyAsync(d_ops.p, ops.data(), ops.size() * sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemcpyAsync(d_gops.p, gops.data(), 3 * sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
-    CK(ctx->w64.alloc(n * n_ops * n_l));
-    CK(ctx->delta.alloc(n));
+    if (presolved && solver != RBF_SOLVER_ACM) return fail(ctx, RBF_EINVAL, "presolved weights: ACM only");
     CK(ctx->status.zero(ctx->st));
-    CK(launch_weights(n, ctx->xyz.p, nullptr, ctx->iota.p, 1, n_l, ctx->idx.p, phs_k, mono_m, n_ops, d_ops.p, 1,
-                      ctx->w64.p, ctx->delta.p, ctx->status.p, ctx->st));
-    ++ctx->launches;
+    if (!presolved) {
+        CK(ctx->w64.alloc(n * n_ops * n_l));
+        CK(ctx->delta.alloc(n));
+        CK(launch_weights(n, ctx->xyz.p, nullptr, ctx->iota.p, 1, n_l, ctx->idx.p, phs_k, mono_m, n_ops, d_ops.p, 1,
+                          ctx->w64.p, ctx->delta.p, ctx->status.p, ctx->st));
+        ++ctx->launches;
+        CK(ctx->wgb64.alloc(nb * 3 * n_l));
+    }
     CK(ctx->wgw64.alloc(nb * 3 * n_l));
-    CK(ctx->wgb64.alloc(nb * 3 * n_l));
     if (nb > 0) {
         if (solver == RBF_SOLVER_ACM) {
             k_gather_wrows<<<nblk(nb * 3 * n_l), 256, 0, ctx->st>>>(nb, n_l, 4, ctx->wall.p, ctx->w64.p, ctx->wgw64.p);
             ++ctx->launches;
-            CK(launch_weights(nb, ctx->xyz.p, nullptr, ctx->wall.p, 1, n_l, ctx->idxb.p, phs_k, mono_m, 3, d_gops.p, 1,
-                              ctx->wgb64.p, nullptr, ctx->status.p + 1, ctx->st));
+            if (!presolved)
+                CK(launch_weights(nb, ctx->xyz.p, nullptr, ctx->wall.p, 1, n_l, ctx->idxb.p, phs_k, mono_m, 3, d_gops.p,
+                                  1, ctx->wgb64.p, nullptr, ctx->status.p + 1, ctx->st));
         } else {
             CK(launch_weights(nb, ctx->xyz.p, nullptr, ctx->wall.p, 1, n_l, ctx->idxw.p, phs_k, mono_m, 3, d_gops.p, 1,
                               ctx->wgw64.p, nullptr, ctx->status.p + 1, ctx->st));
@@ -498,12 +509,18 @@ int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, 
     ctx->m_p = 0;
     if (rep) {
         rep->n_systems = n + nb;
-        rep->n_singular = sing[0] + sing[1];
+        rep->n_singular = sing[0] + sing[1] + ext_sing;
         rep->h_min = hmin;
     }
-    if (sing[0] + sing[1] > 0) return fail(ctx, RBF_ESINGULAR, "rbf_compute_weights: singular stencil systems");
+    if (sing[0] + sing[1] + ext_sing > 0) return fail(ctx, RBF_ESINGULAR, "rbf_compute_weights: singular stencil systems");
     ctx->weights_ok = true;
     return RBF_OK;
+}
+
+extern "C" {
+
+int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, double dx, rbf_weight_report *rep) {
+    return compute_weights_impl(ctx, phs_k, mono_m, solver, q, dx, rep, false, 0);
 }
 
 int rbf_get_weights(rbf_ctx *ctx, int op, double *out) {
@@ -935,6 +952,94 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
     return RBF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Steady ACM solve of one or more initialised contexts (same device, stream,
+// precision and n_p) in one persistent cooperative launch.  Per cell: steps taken,
+// last residual, status (1 converged, 0 step cap, 3 non-finite).
+template <typename T>
+int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_solve_opts *o, std::vector<int64_t> &steps,
+                       std::vector<double> &resid, std::vector<int32_t> &done, std::string &err) {
+    rbf_ctx *ctx = cs[0];  // for CK's error reporting
+    const int nc = (int)cs.size();
+    std::vector<CellDesc<T>> desc(nc);
+    std::vector<int2> sl, wsl;
+    for (int c = 0; c < nc; ++c) {
+        rbf_ctx *x = cs[c];
+        DevArr<T> *a = nullptr;
+        const DevArr<T> *ws = nullptr, *wn = nullptr;
+        if constexpr (sizeof(T) == 4) { a = x->a32; ws = &x->ws32; wn = &x->wn32; }
+        else { a = x->a64; ws = &x->ws64; wn = &x->wn64; }
+        CellDesc<T> &d = desc[c];
+        std::memset(&d, 0, sizeof(d));
+        d.n = x->n; d.nb = x->nb; d.n_l = x->n_l; d.parity0 = x->parity;
+        d.idx = x->idx_sell.p; d.w = ws->p; d.type = x->type.p; d.wall = x->wall.p; d.idxb = x->idxb_sell.p; d.wn = wn->p;
+        d.u = a[0].p; d.v = a[1].p; d.w_ = a[2].p; d.p = a[3].p; d.us = a[4].p; d.vs = a[5].p; d.ws = a[6].p;
+        d.uo = a[7].p; d.vo = a[8].p; d.wo = a[9].p; d.vmax = x->vmax.p;
+        d.dt = (T)x->dt; d.nu = (T)x->prm.nu; d.gx = (T)x->prm.g[0]; d.gy = (T)x->prm.g[1]; d.gz = (T)x->prm.g[2];
+        d.rho = (T)x->rho; d.beta = x->beta; d.vref = x->vref;
+        for (int64_t s = 0; s < x->npad / 32; ++s) sl.push_back(make_int2(c, (int)s));
+        for (int64_t s = 0; s < (x->nb + 31) / 32; ++s) wsl.push_back(make_int2(c, (int)s));
+    }
+    int maxb = 0;
+    CK(acm_persistent_max_blocks<T>(&maxb));
+    const int nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + 7) / 8)));
+    DevArr<CellDesc<T>> d_desc;
+    DevArr<int2> d_sl, d_wsl;
+    DevArr<unsigned> d_bar;
+    DevArr<int32_t> d_err, d_done;
+    DevArr<int64_t> d_steps;
+    DevArr<double> d_res, d_part;
+    CK(d_desc.alloc(nc)); CK(d_sl.alloc(sl.size())); CK(d_wsl.alloc(std::max<size_t>(wsl.size(), 1)));
+    CK(d_bar.alloc(2)); CK(d_err.alloc(1)); CK(d_done.alloc(nc)); CK(d_steps.alloc(nc)); CK(d_res.alloc(nc));
+    CK(d_part.alloc((size_t)nblocks * 2 * PERSIST_MAX_CELLS));
+    CK(cudaMemcpyAsync(d_desc.p, desc.data(), nc * sizeof(CellDesc<T>), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sl.p, sl.data(), sl.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    if (!wsl.empty()) CK(cudaMemcpyAsync(d_wsl.p, wsl.data(), wsl.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(d_bar.zero(st)); CK(d_err.zero(st)); CK(d_done.zero(st)); CK(d_steps.zero(st)); CK(d_res.zero(st));
+    PersistCtl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    ctl.bar_count = d_bar.p; ctl.bar_gen = d_bar.p + 1; ctl.err = d_err.p; ctl.done = d_done.p; ctl.steps = d_steps.p;
+    ctl.resid = d_res.p; ctl.partial = d_part.p; ctl.ncells = nc; ctl.nslices = (int64_t)sl.size();
+    ctl.nwslices = (int64_t)wsl.size(); ctl.slices = d_sl.p; ctl.wslices = d_wsl.p; ctl.max_steps = o->max_steps;
+    ctl.check_every = o->check_every > 0 ? o->check_every : 100; ctl.tol = o->tol; ctl.n_p = cs[0]->n_p;
+    CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, st));
+    for (rbf_ctx *x : cs) x->launches += 1;
+    CK(cudaStreamSynchronize(st));
+    int32_t e = 0;
+    steps.assign(nc, 0); resid.assign(nc, 0.0); done.assign(nc, 0);
+    CK(cudaMemcpy(&e, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(steps.data(), d_steps.p, nc * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(resid.data(), d_res.p, nc * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(done.data(), d_done.p, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < nc; ++c) {
+        cs[c]->parity = (int)((cs[c]->parity + (int64_t)cs[c]->n_p * steps[c]) & 1);
+        drop_graph(cs[c]);
+    }
+    if (e) {
+        err = "persistent ACM driver: a grid barrier timed out";
+        return RBF_ETIMEOUT;
+    }
+    return RBF_OK;
+}
+
+int persistent_solve(std::vector<rbf_ctx *> &cs, const rbf_solve_opts *o, std::vector<int64_t> &steps,
+                     std::vector<double> &resid, std::vector<int32_t> &done, std::string &err) {
+    for (rbf_ctx *x : cs)
+        if (!x->inited || x->solver != RBF_SOLVER_ACM || x->prec != cs[0]->prec || x->n_p != cs[0]->n_p ||
+            x->device != cs[0]->device)
+            return RBF_EINVAL;
+    if ((int)cs.size() > PERSIST_MAX_CELLS) return RBF_EINVAL;
+    if (cs[0]->prec == RBF_FP32) return persistent_solve_T<float>(cs, cs[0]->st, o, steps, resid, done, err);
+    return persistent_solve_T<double>(cs, cs[0]->st, o, steps, resid, done, err);
+}
+
+}  // namespace
+
+extern "C" {
+
 int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
     if (!ctx || !opts || !res) return RBF_EINVAL;
     if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_solve: not initialised");
@@ -945,6 +1050,26 @@ int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
     std::memset(res, 0, sizeof(*res));
     double kprev = NAN;
     int64_t done = 0;
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        std::vector<rbf_ctx *> cs{ctx};
+        std::vector<int64_t> st;
+        std::vector<double> rs;
+        std::vector<int32_t> dn;
+        std::string msg;
+        rbf_solve_opts o = *opts;
+        o.check_every = every;
+        const int rc = persistent_solve(cs, &o, st, rs, dn, msg);
+        if (rc) return fail(ctx, rc, msg.empty() ? std::string("rbf_solve: persistent driver failed: ") + ctx->err : msg);
+        res->steps = st[0];
+        res->residual = rs[0];
+        res->converged = dn[0] == 1;
+        if (dn[0] == 3) return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite velocity");
+        double k = 0.0;
+        int rc2 = rbf_permeability(ctx, m_p, &k, nullptr);
+        if (rc2) return rc2;
+        res->k_over_d2 = k;
+        return res->converged ? RBF_OK : fail(ctx, RBF_ENOTCONVERGED, "rbf_solve: step cap reached");
+    }
     while (done < opts->max_steps) {
         int64_t chunk = std::min<int64_t>(every, opts->max_steps - done);
         double crit = NAN;
@@ -1096,3 +1221,192 @@ extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2,
     if (k_over_d2) *k_over_d2 = gmag > 0.0 ? qq * ctx->prm.nu / gmag : 0.0;
     return RBF_OK;
 }
+
+// ===========================================================================
+// Batched cells: many periodic cells (own nodes, sphere and stencil size) whose
+// weight systems are solved in one launch and whose ACM steps run in one
+// persistent launch until each cell's criterion holds.
+struct rbf_batch {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<rbf_ctx *> cells;
+    std::vector<int> n_l;
+    bool built = false;
+};
+
+namespace {
+int bfail(rbf_batch *b, int code, const std::string &m) {
+    if (b) b->err = m;
+    return code;
+}
+}  // namespace
+
+extern "C" {
+
+int rbf_batch_create(rbf_batch **out, int device, void *cuda_stream) {
+    if (!out) return RBF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RBF_ECUDA;
+    rbf_batch *b = new rbf_batch();
+    b->device = device;
+    DeviceGuard dg(device);
+    if (cuda_stream) b->st = (cudaStream_t)cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) { delete b; return RBF_ECUDA; }
+        b->own_stream = true;
+    }
+    *out = b;
+    return RBF_OK;
+}
+
+int rbf_batch_destroy(rbf_batch *b) {
+    if (!b) return RBF_EINVAL;
+    for (rbf_ctx *c : b->cells) rbf_destroy(c);
+    {
+        DeviceGuard dg(b->device);
+        if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    }
+    delete b;
+    return RBF_OK;
+}
+
+const char *rbf_batch_last_error(const rbf_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int rbf_batch_add_cell(rbf_batch *b, int64_t n, const double *xyz, const uint8_t *type, const double *normal,
+                       const double c[3], double r, int n_l) {
+    if (!b) return RBF_EINVAL;
+    if ((int)b->cells.size() >= PERSIST_MAX_CELLS) return bfail(b, RBF_EINVAL, "rbf_batch_add_cell: at most 128 cells");
+    rbf_ctx *x = nullptr;
+    int rc = rbf_create(&x, b->device, b->st);
+    if (rc) return bfail(b, rc, "rbf_batch_add_cell: context creation failed");
+    rc = rbf_set_nodes(x, n, xyz, type, normal);
+    if (!rc) rc = rbf_set_sphere(x, c, r);
+    if (rc) {
+        b->err = x->err;
+        rbf_destroy(x);
+        return rc;
+    }
+    if (n_l < 2 || n_l > RBF_MAX_NL) { rbf_destroy(x); return bfail(b, RBF_EINVAL, "rbf_batch_add_cell: bad n_l"); }
+    b->cells.push_back(x);
+    b->n_l.push_back(n_l);
+    b->built = false;
+    return (int)b->cells.size() - 1;
+}
+
+int rbf_batch_build(rbf_batch *b, int phs_k, int mono_m, rbf_weight_report *rep) {
+    if (!b) return RBF_EINVAL;
+    if (b->cells.empty()) return bfail(b, RBF_EINVAL, "rbf_batch_build: no cells");
+    if (phs_k < 3 || phs_k % 2 == 0 || phs_k > 9 || mono_m < 0 || mono_m > 4) return bfail(b, RBF_EINVAL, "rbf_batch_build: bad k or m");
+    DeviceGuard dg(b->device);
+    const int nc = (int)b->cells.size();
+    int max_nl = 0;
+    for (int c = 0; c < nc; ++c) {
+        int rc = rbf_build_stencils(b->cells[c], b->n_l[c]);
+        if (rc) return bfail(b, rc, std::string("cell ") + std::to_string(c) + ": " + b->cells[c]->err);
+        if (b->n_l[c] < binom(mono_m + 3, 3)) return bfail(b, RBF_EINVAL, "rbf_batch_build: n_l < N_p");
+        max_nl = std::max(max_nl, b->n_l[c]);
+    }
+    // the node systems of every cell in one launch, then the wall Neumann systems of every cell in one launch
+    std::vector<WeightJob> nodes(nc), walls;
+    std::vector<int64_t> pn(nc + 1, 0), pw(1, 0);
+    for (int c = 0; c < nc; ++c) {
+        rbf_ctx *ctx = b->cells[c];
+        CK(ctx->w64.alloc(ctx->n * 4 * ctx->n_l));
+        CK(ctx->delta.alloc(ctx->n));
+        CK(ctx->wgb64.alloc(ctx->nb * 3 * ctx->n_l));
+        nodes[c] = WeightJob{ctx->n, ctx->xyz.p, ctx->iota.p, ctx->n_l, ctx->idx.p, ctx->w64.p, ctx->delta.p};
+        pn[c + 1] = pn[c] + ctx->n;
+        if (ctx->nb > 0) {
+            walls.push_back(WeightJob{ctx->nb, ctx->xyz.p, ctx->wall.p, ctx->n_l, ctx->idxb.p, ctx->wgb64.p, nullptr});
+            pw.push_back(pw.back() + ctx->nb);
+        }
+    }
+    rbf_ctx *ctx = b->cells[0];  // for CK
+    std::vector<OpSpec> ops, gops;
+    for (int kind : {OP_DX, OP_DY, OP_DZ, OP_LAP}) ops.push_back(OpSpec{kind, {0.0, 0.0, 0.0}});
+    for (int kind : {OP_DX, OP_DY, OP_DZ}) gops.push_back(OpSpec{kind, {0.0, 0.0, 0.0}});
+    DevArr<WeightJob> dj, dwj;
+    DevArr<int64_t> dpn, dpw;
+    DevArr<OpSpec> dops, dgops;
+    DevArr<int32_t> dsing;
+    CK(dj.alloc(nc)); CK(dpn.alloc(nc + 1)); CK(dops.alloc(4)); CK(dgops.alloc(3)); CK(dsing.alloc(2));
+    CK(cudaMemcpyAsync(dj.p, nodes.data(), nc * sizeof(WeightJob), cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(dpn.p, pn.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(dops.p, ops.data(), 4 * sizeof(OpSpec), cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(dgops.p, gops.data(), 3 * sizeof(OpSpec), cudaMemcpyHostToDevice, b->st));
+    CK(dsing.zero(b->st));
+    CK(launch_weights_multi(nc, dj.p, dpn.p, pn[nc], max_nl, phs_k, mono_m, 4, dops.p, 1, dsing.p, b->st));
+    if (!walls.empty()) {
+        CK(dwj.alloc(walls.size())); CK(dpw.alloc(pw.size()));
+        CK(cudaMemcpyAsync(dwj.p, walls.data(), walls.size() * sizeof(WeightJob), cudaMemcpyHostToDevice, b->st));
+        CK(cudaMemcpyAsync(dpw.p, pw.data(), pw.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->st));
+        CK(launch_weights_multi((int)walls.size(), dwj.p, dpw.p, pw.back(), max_nl, phs_k, mono_m, 3, dgops.p, 1,
+                                dsing.p + 1, b->st));
+    }
+    int32_t sing[2] = {0, 0};
+    CK(cudaMemcpyAsync(sing, dsing.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    int64_t nsys = 0, nsing = sing[0] + sing[1];
+    double hmin = 1e300;
+    for (int c = 0; c < nc; ++c) {
+        rbf_weight_report r;
+        const int rc = compute_weights_impl(b->cells[c], phs_k, mono_m, RBF_SOLVER_ACM, 0, 0.0, &r, true, c == 0 ? nsing : 0);
+        nsys += r.n_systems;
+        hmin = std::min(hmin, r.h_min);
+        if (rc) {
+            if (rep) { rep->n_systems = nsys; rep->n_singular = nsing; rep->h_min = hmin; }
+            return bfail(b, rc, std::string("cell ") + std::to_string(c) + ": " + b->cells[c]->err);
+        }
+    }
+    if (rep) { rep->n_systems = nsys; rep->n_singular = nsing; rep->h_min = hmin; }
+    b->built = true;
+    return RBF_OK;
+}
+
+int rbf_batch_init(rbf_batch *b, const rbf_params *p) {
+    if (!b || !p) return RBF_EINVAL;
+    if (!b->built) return bfail(b, RBF_EINVAL, "rbf_batch_init: build first");
+    for (size_t c = 0; c < b->cells.size(); ++c) {
+        const int rc = rbf_init(b->cells[c], p);
+        if (rc) return bfail(b, rc, b->cells[c]->err);
+    }
+    return RBF_OK;
+}
+
+int rbf_batch_solve(rbf_batch *b, const rbf_solve_opts *opts, rbf_batch_cell_result *res) {
+    if (!b || !opts || !res) return RBF_EINVAL;
+    if (b->cells.empty() || !b->cells[0]->inited) return bfail(b, RBF_EINVAL, "rbf_batch_solve: init first");
+    if (opts->max_steps < 1 || !(opts->tol > 0.0)) return bfail(b, RBF_EINVAL, "rbf_batch_solve: bad options");
+    DeviceGuard dg(b->device);
+    std::vector<int64_t> st;
+    std::vector<double> rs;
+    std::vector<int32_t> dn;
+    std::string msg;
+    const int rc = persistent_solve(b->cells, opts, st, rs, dn, msg);
+    if (rc) return bfail(b, rc, msg.empty() ? "rbf_batch_solve: persistent driver failed" : msg);
+    const int m_p = opts->m_p > 0 ? opts->m_p : 32;
+    bool all = true;
+    for (size_t c = 0; c < b->cells.size(); ++c) {
+        res[c].steps = st[c];
+        res[c].residual = rs[c];
+        res[c].status = dn[c] == 1 ? 0 : (dn[c] == 3 ? 2 : 1);
+        all &= dn[c] == 1;
+        double k = 0.0;
+        const int r2 = rbf_permeability(b->cells[c], m_p, &k, nullptr);
+        if (r2) return bfail(b, r2, b->cells[c]->err);
+        res[c].k_over_d2 = k;
+    }
+    return all ? RBF_OK : bfail(b, RBF_ENOTCONVERGED, "rbf_batch_solve: not every cell converged");
+}
+
+int rbf_batch_num_cells(const rbf_batch *b) { return b ? (int)b->cells.size() : -1; }
+
+rbf_ctx *rbf_batch_cell(rbf_batch *b, int cell) {
+    if (!b || cell < 0 || cell >= (int)b->cells.size()) return nullptr;
+    return b->cells[cell];
+}
+
+}  // extern "C"

@@ -80,6 +80,21 @@ cudaError_t launch_weights(int64_t nc, const double *xyz, const double *cxyz, co
                            const OpSpec *ops, int refine, double *w, double *delta, int32_t *n_sing,
                            cudaStream_t st);
 
+// one entry of a multi-set weight launch: nc centres, centre c = node cnode[c] of
+// xyz with stencil idx[c * n_l ..] -> w[(c * n_ops + o) * n_l + j], delta[c]
+struct WeightJob {
+    int64_t nc;
+    const double *xyz;
+    const int32_t *cnode;
+    int n_l;
+    const int32_t *idx;
+    double *w;
+    double *delta;
+};
+cudaError_t launch_weights_multi(int njobs, const WeightJob *jobs_dev, const int64_t *prefix_dev, int64_t ntot,
+                                 int max_n_l, int k, int m, int n_ops, const OpSpec *ops, int refine, int32_t *n_sing,
+                                 cudaStream_t st);
+
 // pack.cu (in weights.cu): FP64 row weights [c][o][j] -> SELL T [s][o][j][lane]
 cudaError_t launch_pack_f32(int64_t nc, int n_ops, int o0, int n_out, int n_l, const double *w, float *ws,
                             cudaStream_t st);

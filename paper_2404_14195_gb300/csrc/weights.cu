@@ -99,18 +99,17 @@ __host__ __device__ inline WLayout wlayout(int n_l, int np, int n_ops) {
     return L;
 }
 
-__global__ void k_weights(int64_t nc, const double *__restrict__ xyz, const double *__restrict__ cxyz,
-                          const int32_t *__restrict__ cnode, int centre_is_node, int n_l,
-                          const int32_t *__restrict__ idx, int k, int m, int np, int n_ops,
-                          const OpSpec *__restrict__ ops, int refine, double *__restrict__ wout,
-                          double *__restrict__ delta_out, int32_t *n_sing) {
-    extern __shared__ double smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
-    if (c >= nc) return;
+// One stencil's saddle system and its right-hand sides, by one warp; `smem_w` is
+// the warp's shared-memory region (at least wlayout(n_l, np, n_ops).per_warp doubles).
+__device__ void weights_one(int64_t c, double *smem_w, const double *__restrict__ xyz, const double *__restrict__ cxyz,
+                            const int32_t *__restrict__ cnode, int centre_is_node, int n_l,
+                            const int32_t *__restrict__ idx, int k, int np, int n_ops,
+                            const OpSpec *__restrict__ ops, int refine, double *__restrict__ wout,
+                            double *__restrict__ delta_out, int32_t *n_sing) {
+    const int lane = threadIdx.x & 31;
     const WLayout L = wlayout(n_l, np, n_ops);
     const int ns = L.ns, ld = L.ld;
-    double *M = smem + warp * L.per_warp;
+    double *M = smem_w;
     double *M0 = M + (size_t)ns * ld;
     double *X = M0 + (size_t)ns * ld;       // [r][o]
     double *R = X + (size_t)ns * n_ops;     // [r][o]
@@ -228,6 +227,56 @@ __global__ void k_weights(int64_t nc, const double *__restrict__ xyz, const doub
         int o = e / n_l, j = e - o * n_l;
         wout[(c * n_ops + o) * n_l + j] = X[j * n_ops + o];
     }
+}
+
+__global__ void k_weights(int64_t nc, const double *__restrict__ xyz, const double *__restrict__ cxyz,
+                          const int32_t *__restrict__ cnode, int centre_is_node, int n_l,
+                          const int32_t *__restrict__ idx, int k, int m, int np, int n_ops,
+                          const OpSpec *__restrict__ ops, int refine, double *__restrict__ wout,
+                          double *__restrict__ delta_out, int32_t *n_sing) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (c >= nc) return;
+    (void)m;
+    weights_one(c, smem + warp * wlayout(n_l, np, n_ops).per_warp, xyz, cxyz, cnode, centre_is_node, n_l, idx, k, np,
+                n_ops, ops, refine, wout, delta_out, n_sing);
+}
+
+// Many stencil sets (e.g. the nodes of many cells, each with its own N_L) in one
+// launch: warp t solves centre t of the concatenation of the jobs.
+__global__ void k_weights_multi(int njobs, const WeightJob *__restrict__ jobs, const int64_t *__restrict__ prefix,
+                                int64_t ntot, size_t per_warp, int k, int np, int n_ops, const OpSpec *__restrict__ ops,
+                                int refine, int32_t *n_sing) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (t >= ntot) return;
+    int j = 0;
+    while (j + 1 < njobs && prefix[j + 1] <= t) ++j;
+    const WeightJob jb = jobs[j];
+    weights_one(t - prefix[j], smem + warp * per_warp, jb.xyz, nullptr, jb.cnode, 1, jb.n_l, jb.idx, k, np, n_ops, ops,
+                refine, jb.w, jb.delta, n_sing);
+}
+
+cudaError_t launch_weights_multi(int njobs, const WeightJob *jobs_dev, const int64_t *prefix_dev, int64_t ntot,
+                                 int max_n_l, int k, int m, int n_ops, const OpSpec *ops, int refine, int32_t *n_sing,
+                                 cudaStream_t st) {
+    if (ntot <= 0) return cudaSuccess;
+    if (n_ops < 1 || n_ops > RBF_MAX_OPS || max_n_l < 2 || max_n_l > RBF_MAX_NL || m < 0 || m > 4) return cudaErrorInvalidValue;
+    const int np = (m + 1) * (m + 2) * (m + 3) / 6;
+    const WLayout L = wlayout(max_n_l, np, n_ops);
+    const size_t per_warp_bytes = L.per_warp * sizeof(double);
+    int warps = (int)((200 * 1024) / per_warp_bytes);
+    if (warps > 4) warps = 4;
+    if (warps < 1) return cudaErrorInvalidValue;
+    const size_t smem = per_warp_bytes * warps;
+    cudaError_t e = cudaFuncSetAttribute(k_weights_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_weights_multi<<<(unsigned)((ntot + warps - 1) / warps), 32 * warps, smem, st>>>(njobs, jobs_dev, prefix_dev, ntot,
+                                                                                     L.per_warp, k, np, n_ops, ops,
+                                                                                     refine, n_sing);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_weights(int64_t nc, const double *xyz, const double *cxyz, const int32_t *cnode,
