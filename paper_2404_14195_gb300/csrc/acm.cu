@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_acm_predict(AcmArgs<T> a) {
     const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
     const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
     T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+#pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
         int q = __ldg(ip + (j << 5));
         T wx = __ldg(wp + (j << 5)), wy = __ldg(wp + ((n_l + j) << 5));
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__r
     const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
     const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
     T div = 0;
+#pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
         int q = __ldg(ip + (j << 5));
         T wx = __ldg(wp + (j << 5)), wy = __ldg(wp + ((n_l + j) << 5)), wz = __ldg(wp + ((2 * n_l + j) << 5));
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(256) k_acm_wall_pressure(AcmArgs<T> a) {
     const int32_t *__restrict__ ip = a.idxb + ((s * n_l) << 5) + lane;
     const T *__restrict__ wp = a.wn + ((s * n_l) << 5) + lane;
     T acc = 0;
+#pragma unroll 4
     for (int j = 1; j < n_l; ++j) acc += __ldg(wp + (j << 5)) * a.p[__ldg(ip + (j << 5))];
     a.p[a.wall[b]] = -acc / __ldg(wp);
 }
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slo
             const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
             const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
             T gx = 0, gy = 0, gz = 0;
-            for (int j = 0; j < n_l; ++j) {
+        #pragma unroll 5
+    for (int j = 0; j < n_l; ++j) {
                 T pq = a.p[__ldg(ip + (j << 5))];
                 gx += __ldg(wp + (j << 5)) * pq;
                 gy += __ldg(wp + ((n_l + j) << 5)) * pq;

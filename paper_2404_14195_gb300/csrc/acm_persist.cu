@@ -70,6 +70,7 @@ __device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool s
     const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
     T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+#pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
         const int q = ip[j << 5];
         const T wx = wp[j << 5], wy = wp[(n_l + j) << 5], wz = wp[(2 * n_l + j) << 5], wl = wp[(3 * n_l + j) << 5];
@@ -98,6 +99,7 @@ __device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool 
     const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
     T div = 0;
+#pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
         const int q = ip[j << 5];
         div += wp[j << 5] * u[q] + wp[(n_l + j) << 5] * v[q] + wp[(2 * n_l + j) << 5] * w[q];
@@ -114,6 +116,7 @@ __device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
     const int32_t *__restrict__ ip = c.idxb + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.wn + ((ls * n_l) << 5) + lane;
     T acc = 0;
+#pragma unroll 4
     for (int j = 1; j < n_l; ++j) acc += wp[j << 5] * c.p[ip[j << 5]];
     c.p[c.wall[b]] = -acc / wp[0];
 }
@@ -127,6 +130,7 @@ __device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
     const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
     T gx = 0, gy = 0, gz = 0;
+#pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
         const T pq = c.p[ip[j << 5]];
         gx += wp[j << 5] * pq;
