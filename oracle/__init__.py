@@ -59,6 +59,7 @@ def _load():
                 "orc_acm_run": [I64, P, P, I, P, P, I64, P, P, P, P, I, I, P, P, P, P, P],
                 "orc_lbm_collide": [I64, I, P, P, P, D, D, P, P, P],
                 "orc_lbm_stream": [I64, I, P, P, P, P, I, P, P, P, P],
+                "orc_lbm_stream_rows": [I64, I64, I, P, P, P, P, I, P, P, P, P, P],
                 "orc_lbm_run": [I64, I, P, P, P, P, P, I, P, P, D, D, P, I, P],
                 "orc_lbm_macro": [I64, I, P, P, P],
                 "orc_apply": [I64, I, P, I, P, P, P],
@@ -277,6 +278,20 @@ def lbm_stream(fpost, q: int, case, idx, wk):
     _load().orc_lbm_stream(n, q, _p(e), _p(opp), _p(np.ascontiguousarray(case["type"], np.uint8)),
                            _p(_f64(case["normal"])), idx.shape[1], _p(_i32(idx)), _p(_f64(wk)),
                            _p(fpost), _p(out))
+    return out
+
+
+def lbm_stream_rows(fpost, q: int, case, rows, idx_rows, wk_rows):
+    """Streaming (with bounce-back) of the selected nodes `rows` only, from the
+    whole post-collision field fpost (q, n); returns (q, len(rows))."""
+    fpost = _f64(fpost)
+    rows = np.ascontiguousarray(rows, np.int64)
+    e, _, opp = velocity_set(q)
+    out = np.empty((q, len(rows)))
+    typ = np.ascontiguousarray(np.asarray(case["type"])[rows], np.uint8)
+    nrm = _f64(np.asarray(case["normal"])[rows])
+    _load().orc_lbm_stream_rows(len(rows), fpost.shape[1], q, _p(e), _p(opp), _p(typ), _p(nrm), idx_rows.shape[1],
+                                _p(_i32(idx_rows)), _p(rows), _p(_f64(wk_rows)), _p(fpost), _p(out))
     return out
 
 

@@ -517,6 +517,34 @@ int orc_lbm_stream(int64_t n, int q, const double *e, const int *opp, const uint
     return 0;
 }
 
+/* The streaming step (with bounce-back) of `nrows` selected nodes only: row r is
+ * node rows[r], its stencil idx (nrows x n_l, node indices into fpost), weights wk
+ * (nrows x q x n_l), type / normal of the selected nodes; fpost (q x n) the whole
+ * post-collision field; f (q x nrows) the streamed populations of the rows.  Same
+ * arithmetic as orc_lbm_stream, for checking large clouds on a sample. */
+int orc_lbm_stream_rows(int64_t nrows, int64_t n, int q, const double *e, const int *opp, const uint8_t *type,
+                        const double *nrm, int n_l, const int32_t *idx, const int64_t *rows, const double *wk,
+                        const double *fpost, double *f) {
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nrows; ++r) {
+        f[r] = fpost[rows[r]];
+        for (int k = 1; k < q; ++k) {
+            const double *wr = wk + (r * q + k) * n_l;
+            double acc = 0.0;
+            for (int j = 0; j < n_l; ++j) acc += wr[j] * fpost[(int64_t)k * n + idx[r * n_l + j]];
+            f[(int64_t)k * nrows + r] = acc;
+        }
+        if (type[r]) {
+            const double *nn = nrm + 3 * r;
+            for (int k = 1; k < q; ++k) {
+                double en = e[3 * k] * nn[0] + e[3 * k + 1] * nn[1] + e[3 * k + 2] * nn[2];
+                if (en > 0.0) f[(int64_t)k * nrows + r] = f[(int64_t)opp[k] * nrows + r];
+            }
+        }
+    }
+    return 0;
+}
+
 /* nsteps of the MLBM algorithm of the appendix (COLLIDE over all nodes, then STREAM
  * over all nodes); f (q x n) holds the pre-collision populations in and out. */
 int orc_lbm_run(int64_t n, int q, const double *e, const double *omega, const int *opp,

@@ -217,3 +217,16 @@ def test_acm_dt_footnote():
     # the MNS section's footnote: dt from 1.25e-6 to 2e-5 for h_min in [0.005, 0.02]
     assert abs(oracle.acm_dt(0.005, 1.0) - 1.25e-6) < 1e-20
     assert abs(oracle.acm_dt(0.02, 1.0) - 2e-5) < 1e-20
+
+
+def test_stream_rows_equals_full_stream():
+    case = synth.jittered_cell(r=0.3, n_axis=9, seed=3)
+    idx = oracle.knn(case["xyz"], case["xyz"], 25)
+    q = 19
+    wk = oracle.lbm_weights(case["xyz"], idx, q, 0.05)
+    rng = np.random.default_rng(0)
+    fpost = rng.random((q, case.n))
+    full = oracle.lbm_stream(fpost, q, case, idx, wk)
+    rows = np.concatenate([np.nonzero(case["type"] == 1)[0][:20], np.arange(0, case.n, 13)])
+    part = oracle.lbm_stream_rows(fpost, q, case, rows, idx[rows], wk[rows])
+    assert np.array_equal(part, full[:, rows])
