@@ -190,7 +190,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--variant", type=int, default=-1,
                     help="LBM step schedule (rbf_set_kernel_variant code); -1 = autotune on the case")
+    ap.add_argument("--workload", default="lbm-config2",
+                    choices=["lbm-config2", "acm-config4", "batch-config3", "mlp-train"],
+                    help="lbm-config2 (default, the headline); acm-config4: ~3M-node ACM cell, r^5, m=3, N_L=40, "
+                         "FP32; batch-config3: 64-cell porosity sweep in one persistent launch; mlp-train: "
+                         "warm-start network training steps on the tensor cores")
+    ap.add_argument("--cfg4-ramp", type=float, default=0.32, help="acm-config4 refinement ramp (0.32: ~3M nodes)")
+    ap.add_argument("--cells", type=int, default=64, help="batch-config3: number of cells")
     args = ap.parse_args()
+    if args.workload != "lbm-config2":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:
@@ -300,6 +309,293 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# further workloads (same JSON line; `metric` names what is measured)
+# ---------------------------------------------------------------------------
+CFG4 = dict(r=0.45, h_min=0.003, h_max=0.02, seed=4, n_l=40, k=5, m=3)
+
+
+def acm_bytes(n_l):
+    """Algorithmic bytes per ACM node-step, FP32 fields and weights: predictor
+    20 N_L + 24, pressure 16 N_L + 20 (x3), correction 16 N_L + 28 (x3)."""
+    return 116 * n_l + 168
+
+
+def _make_cell3(args):
+    r, hmin, seed, n_l = args
+    import synth
+    c = synth.refined_cell(r=r, h_min=hmin, h_max=0.04, ramp=0.2, seed=seed)
+    return c, n_l
+
+
+def config3_cells(ncells, seed=3):
+    """Config 3: radii U[0.15, 0.62], h_min U[0.006, 0.012], h_max 0.04, the
+    config-2 ramp, N_L U{20..45}; generated in a spawn pool (before any GPU use)."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(seed)
+    jobs = [(float(rng.uniform(0.15, 0.62)), float(rng.uniform(0.006, 0.012)), 1000 + i, int(rng.integers(20, 46)))
+            for i in range(ncells)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        return pool.map(_make_cell3, jobs)
+
+
+def _timed(fn, local, dist):
+    import torch
+    with Clocks(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist is not None:
+            dist.barrier()
+    return wall, clk.summary()
+
+
+def run_workload(args):
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return _reference_workload(args)
+    cells3 = config3_cells(args.cells) if args.workload == "batch-config3" else None
+    import torch
+    import paper_2404_14195_gb300 as rbf
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    rbf._build.build()
+    peaks = measured_peaks()
+    if args.workload == "acm-config4":
+        line = _acm_config4(args, rbf, local, dist, ws, peaks)
+    elif args.workload == "batch-config3":
+        line = _batch_config3(args, rbf, local, dist, ws, peaks, cells3)
+    else:
+        line = _mlp_train(args, rbf, local, dist, ws, peaks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _max_over_ranks(x, dist):
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _acm_config4(args, rbf, local, dist, ws, peaks):
+    import synth
+    import torch
+    c = CFG4
+    case = synth.refined_cell(r=c["r"], h_min=c["h_min"], h_max=c["h_max"], ramp=args.cfg4_ramp, seed=c["seed"])
+    n, nb = case.n, int((case["type"] == 1).sum())
+    s = rbf.Solver(local)
+    s.set_case(case)
+    s.build_stencils(c["n_l"])
+    t0 = time.perf_counter()
+    rep = s.compute_weights(k=c["k"], m=c["m"], solver=rbf.RBF_SOLVER_ACM)
+    t_w = time.perf_counter() - t0
+    s.init(precision=rbf.RBF_FP32, v_ref=0.01)
+    tune, chosen = s.autotune(10)
+    s.step(args.warmup)
+    l0 = s.launch_count()
+    holder = {}
+
+    def work():
+        s.step(args.steps)
+        holder["ms"] = s.last_step_timing()[0]
+
+    wall, clk = _timed(work, local, dist)
+    launches = s.launch_count() - l0
+    tmax = _max_over_ranks(holder["ms"], dist)
+    prof = s.profile_steps(10)  # predictor, pressure, wall pressure, correction
+    L = c["n_l"]
+    kb = {"predict": (20 * L + 24) * n, "pressure": (16 * L + 20) * n, "wall_pressure": (8 * L + 8) * nb,
+          "correct": (16 * L + 28) * n}
+    names = list(kb)
+    share = {nm: prof[i] * (1 if i == 0 else 3) for i, nm in enumerate(names)}
+    dom = max(share, key=share.get)
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    per_kernel = {nm: {"ms": float(prof[i]), "GB/s": kb[nm] / (prof[i] / 1e3) / 1e9} for i, nm in enumerate(names)}
+    ach = per_kernel[dom]["GB/s"]
+    step_gbs = acm_bytes(L) * n / (tmax / args.steps / 1e3) / 1e9
+    # e2e: host fields in, one step, fields out, every step
+    f_host = torch.empty((n, 4), dtype=torch.float64, pin_memory=True).numpy()
+    f_host[:] = s.get_fields()
+    out = torch.empty((n, 4), dtype=torch.float64, pin_memory=True).numpy()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.set_fields(f_host)
+        s.step(1)
+        out[:] = s.get_fields()
+    e2e = _max_over_ranks(time.perf_counter() - t0, dist)
+    k_perm, _ = s.permeability(32)
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = _oracle_acm_baseline(case, c)
+    return {
+        "metric": "node-steps/s (ACM steps, config 4)", "value": ws * n * args.steps / (tmax / 1e3), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded node cloud)",
+        "config": {"workload": f"ACM FP32 steps, periodic SC cell r={c['r']}, h(d)={c['h_min']}..{c['h_max']} "
+                               f"ramp {args.cfg4_ramp}, N={n} ({nb} wall), N_L={L}, PHS r^{c['k']} + m={c['m']}",
+                   "nodes": n, "wall_nodes": nb, "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}",
+                   "weights_solve_s": t_w, "h_min": rep["h_min"], "acm_block": chosen, "autotune": tune},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "kernel": f"k_acm_{dom}<float>", "per_kernel": per_kernel,
+                     "step_GBs": step_gbs, "step_frac": step_gbs / peak},
+        "cpu_baseline": cpu, "e2e": {"value": ws * n * args.e2e_steps / e2e, "unit": UNIT,
+                                     "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 32 * n},
+        "gpu_launches": int(launches), "clocks": clk, "k_over_d2_after_run": k_perm, "wall_s_timed": wall,
+    }
+
+
+def _oracle_acm_baseline(case, c, budget_s=15.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    idx = oracle.knn(case["xyz"], case["xyz"], c["n_l"], grid=True)
+    w4 = oracle.acm_weights(case["xyz"], idx, c["k"], c["m"])
+    wl, idxb = oracle.neumann_stencils(case, c["n_l"])
+    wgb = oracle.neumann_weights(case, idxb, c["k"], c["m"])
+    t_setup = time.perf_counter() - t0
+    dmin = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
+    dt = oracle.acm_dt(dmin, 1.0)
+    f = np.zeros((case.n, 4))
+    t0 = time.perf_counter()
+    f, _ = oracle.acm_run(case, idx, w4, idxb, wgb, f, 1, dt=dt, v_ref=0.01)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(100, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.acm_run(case, idx, w4, idxb, wgb, f, steps, dt=dt, v_ref=0.01)
+    dt_run = time.perf_counter() - t0
+    return {"value": case.n * steps / dt_run, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle ACM steps of the full {case.n}-node cell "
+                      f"(stencils and weights untimed: {t_setup:.0f} s)"}
+
+
+def _batch_config3(args, rbf, local, dist, ws, peaks, cells):
+    b = rbf.Batch(local)
+    n_tot = 0
+    for case, n_l in cells:
+        b.add_cell(case, n_l)
+        n_tot += case.n
+    t0 = time.perf_counter()
+    rep = b.build(3, 2)
+    t_build = time.perf_counter() - t0
+    b.init(precision=rbf.RBF_FP32, v_ref=0.01)
+    b.solve(args.warmup, 1e-300, check_every=args.warmup)
+    holder = {}
+
+    def work():
+        holder["res"] = b.solve(args.steps, 1e-300, check_every=max(1, args.steps // 4))
+
+    wall, clk = _timed(work, local, dist)
+    tmax = _max_over_ranks(wall, dist)
+    nl = [n_l for _, n_l in cells]
+    byts = sum(acm_bytes(n_l) * case.n for case, n_l in cells)
+    gbs = byts * args.steps / tmax / 1e9
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    return {
+        "metric": "node-steps/s (batched ACM steps, config 3)", "value": ws * n_tot * args.steps / tmax, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded node clouds)",
+        "config": {"workload": f"{len(cells)} periodic SC cells, r~U[0.15,0.62], h_min~U[0.006,0.012], h_max 0.04, "
+                               f"N_L~U{{20..45}}, one persistent launch (wall-clock timed, includes launch and "
+                               f"the per-cell FP64 residual checks)",
+                   "cells": len(cells), "nodes_total": n_tot, "nodes_min": min(c.n for c, _ in cells),
+                   "nodes_max": max(c.n for c, _ in cells), "n_l_range": [min(nl), max(nl)],
+                   "build_s (stencils, one weight launch for all cells, packing)": t_build,
+                   "weight_systems": rep["n_systems"], "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "traffic": None, "kernel": "k_acm_persistent<float> (whole step, all cells)"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": 1, "clocks": clk, "wall_s_timed": wall,
+    }
+
+
+def _mlp_flops_per_sample():
+    # forward 2 * sum(fan_in * fan_out) over the five layers; backward twice that
+    return 3 * 2 * (64 * 128 + 3 * 128 * 128 + 128 * 16)
+
+
+def _mlp_train(args, rbf, local, dist, ws, peaks):
+    from oracle import mlp as om
+    B = 16384
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    xyz = rng.random((n, 3))
+    r = rng.uniform(0.15, 0.62, n).astype(np.float32)
+    sdf = rng.uniform(0.0, 0.4, n).astype(np.float32)
+    tgt = (0.1 * rng.standard_normal((n, 4))).astype(np.float32)
+    m = rbf.Mlp(local)
+    m.set_params(om.init_params(1).astype(np.float32))
+    m.set_data(xyz, r, sdf, tgt)
+    m.train(args.warmup, B, 1e-3, 1)
+    holder = {}
+    l0 = m.launch_count()
+
+    def work():
+        holder["loss"] = m.train(args.steps, B, 1e-3, 1)
+
+    wall, clk = _timed(work, local, dist)
+    tmax = _max_over_ranks(wall, dist)
+    fl = _mlp_flops_per_sample() * B * args.steps / tmax / 1e12
+    peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        th = om.init_params(1)
+        X = om.features(xyz[:B], r[:B], sdf[:B])
+        t0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < 10.0:
+            om.loss_and_grad(th, X, tgt[:B])
+            steps += 1
+        cpu = {"value": steps * B / (time.perf_counter() - t0), "unit": "samples/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"{steps} FP64 numpy forward+backward passes of {B} samples"}
+    return {
+        "metric": "samples/s (warm-start MLP training steps)", "value": ws * B * args.steps / tmax,
+        "unit": "samples/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (fp32 accumulate, fp32 Adam)", "data": "synthetic random samples",
+        "config": {"workload": f"MLP 64-128x4-16 GELU, batch {B}, forward + backward + Adam per step (CUDA graph)",
+                   "batch": B, "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "tensor", "achieved": fl, "peak": peak, "unit": "TFLOP/s", "frac": fl / peak,
+                     "traffic": None, "kernel": "k_gemm (tcgen05) + epilogues, whole training step",
+                     "flops_per_sample": _mlp_flops_per_sample(),
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(m.launch_count() - l0), "clocks": clk,
+        "final_loss": float(holder["loss"][-1]), "wall_s_timed": wall,
+    }
+
+
+def _reference_workload(args):
+    if args.workload == "acm-config4":
+        import synth
+        c = CFG4
+        case = synth.refined_cell(r=c["r"], h_min=c["h_min"], h_max=c["h_max"], ramp=args.cfg4_ramp, seed=c["seed"])
+        base = _oracle_acm_baseline(case, c, budget_s=60.0)
+        metric = "node-steps/s (ACM steps, config 4)"
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": f"no CPU reference leg for {args.workload}"}))
+        return 0
+    print(json.dumps({"metric": metric, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus, "impl": "reference",
+                      "higher_is_better": True, "dtype": "f64", "cpu_baseline": base,
+                      "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
     return 0
 
 
