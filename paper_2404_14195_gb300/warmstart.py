@@ -1,0 +1,67 @@
+"""Learned warm start of the steady ACM solve: training data from steady fields
+the solver itself produces, training of the network, and evaluation against a
+zero start.  Orchestration only: every solve, the training and the inference run
+in the library's kernels (rbf_batch_*, rbf_mlp_*)."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import RBF_FP32, Batch, Mlp, Solver
+
+N_L_DEFAULT = 25
+
+
+def signed_distance(xyz, centre, r):
+    d = np.asarray(xyz, np.float64) - np.asarray(centre, np.float64)
+    d -= np.rint(d)
+    return np.sqrt((d * d).sum(1)) - r
+
+
+def steady_training_set(cases, n_l=N_L_DEFAULT, tol=1e-6, max_steps=2_000_000, check_every=1000,
+                        precision=RBF_FP32, device=0):
+    """Solve every case to steady state in one batched persistent launch; returns
+    (xyz, radius, sdf, targets (u, v, w, p)) over all nodes, the per-cell results
+    and the wall time."""
+    t0 = time.perf_counter()
+    b = Batch(device)
+    for c in cases:
+        b.add_cell(c, n_l)
+    b.build(3, 2)
+    b.init(precision=precision, v_ref=0.01)
+    res = b.solve(max_steps, tol, check_every=check_every)
+    X, R, S, T = [], [], [], []
+    for i, c in enumerate(cases):
+        f = b.cell(i).get_fields()
+        X.append(c["xyz"])
+        R.append(np.full(c.n, c["radius"], np.float32))
+        S.append(signed_distance(c["xyz"], c["centre"], c["radius"]).astype(np.float32))
+        T.append(f.astype(np.float32))
+    b.close()
+    return (np.concatenate(X), np.concatenate(R), np.concatenate(S), np.concatenate(T)), res, time.perf_counter() - t0
+
+
+def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0):
+    m = Mlp(device)
+    m.set_params(np.asarray(init_params, np.float32))
+    m.set_data(*data)
+    t0 = time.perf_counter()
+    hist = m.train(steps, batch, lr, seed)
+    return m, hist, time.perf_counter() - t0
+
+
+def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32, tol=1e-6, max_steps=2_000_000,
+               check_every=1000, m_p=24, device=0):
+    """Steady solve of one case from a zero start or from the network's prediction."""
+    s = Solver(device)
+    s.set_case(case)
+    s.build_stencils(n_l)
+    s.compute_weights(solver=0)
+    s.init(precision=precision, v_ref=0.01)
+    t0 = time.perf_counter()
+    if mlp is not None:
+        mlp.warm_start(s, 1.0)
+    r = s.solve(max_steps, tol, check_every=check_every, m_p=m_p)
+    r["seconds"] = time.perf_counter() - t0
+    return s, r
