@@ -43,7 +43,14 @@ enum {
 };
 
 enum { RBF_SOLVER_ACM = 0, RBF_SOLVER_LBM = 1 };
-enum { RBF_FP64 = 0, RBF_FP32 = 1 };
+/* RBF_FP32C (ACM only): FP32 weights and FP32 stencil arithmetic, with u, v, w
+ * and p carried as pairs of floats hi + lo (compensated summation of every field
+ * update; stencil gathers read hi).  Per-step increments near the steady state
+ * lie far below one float ulp of the fields; plain FP32 rounds them away and the
+ * explicit iteration stalls short of the steady state, the pairs keep them.
+ * rbf_get_fields returns hi + lo; rbf_set_fields splits each value into the
+ * pair. */
+enum { RBF_FP64 = 0, RBF_FP32 = 1, RBF_FP32C = 2 };
 enum { RBF_FLUID = 0, RBF_WALL = 1 };
 /* operator ids for rbf_get_weights */
 enum {
@@ -107,7 +114,7 @@ int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, 
 int rbf_get_weights(rbf_ctx *ctx, int op, double *out);
 
 typedef struct {
-    int precision;   /* RBF_FP64 or RBF_FP32: storage and arithmetic of the steps */
+    int precision;   /* RBF_FP64, RBF_FP32 or RBF_FP32C (ACM): storage and arithmetic of the steps */
     double nu;       /* kinematic viscosity */
     double g[3];     /* body acceleration */
     double rho;      /* density (ACM) / reference density (LBM); 0 -> 1 */
@@ -194,10 +201,17 @@ int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int6
 int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classes);
 
 /* Schedule of the fused LBM step (all compute the same step; only the thread
- * mapping differs): 0 one node per thread, 256-thread blocks; 1 one opposite-
- * population pair per warp, (q-1)/2 warps per 32-node slice, moments reduced in
- * shared memory, stencil loop unrolled 5 deep (default); 2 as 0 with 128-thread
- * blocks; 3, 4, 5 as 1 unrolled 3, 6, 2 deep. */
+ * mapping and the population layout differ): 0 one node per thread, 256-thread
+ * blocks; 1 one opposite-population pair per warp, (q-1)/2 warps per 32-node
+ * slice, moments reduced in shared memory, stencil loop unrolled 5 deep
+ * (default); 2 as 0 with 128-thread blocks; 3, 4, 5 as 1 unrolled 3, 6, 2 deep.
+ * 0-5 keep the populations as the rest population plus interleaved opposite
+ * pairs; 6 and 7 keep each node's q populations in one record of q rounded up
+ * to a multiple of 4 values, read with 16-byte loads: 6 one node per thread,
+ * 256-thread blocks; 7 the same with 128-thread blocks and the stencil loop
+ * unrolled 2 deep.  Switching between the two layouts on an initialised LBM
+ * context rewrites the state (one kernel launch); the populations, as
+ * rbf_lbm_get_populations reports them, are unchanged. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
 
 typedef struct {
@@ -215,6 +229,20 @@ typedef struct {
  * after the trials, so the state and step count are unchanged.  Needs rbf_init;
  * allocates a temporary copy of the state.  2 <= trial_steps <= 2000. */
 int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
+
+/* Autotuner of the persistent ACM driver (rbf_solve): time 256, 128, 64 and 32
+ * threads per block (one 32-node slice per warp; the grid is as many blocks as
+ * cover the slices, at most the co-resident count) over trial_steps steps each,
+ * CUDA events around the cooperative launch, and keep the fastest for this
+ * context's later rbf_solve calls.  Fields and step parity are saved before and
+ * restored after the trials.  ACM contexts only; 2 <= trial_steps <= 20000.
+ * rep->code[c] is the block size of candidate c. */
+int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
+/* Threads per block of the persistent ACM driver for this context (32, 64, 128
+ * or 256; default 256).  A batch launches with its first cell's setting.  The
+ * block size changes only the order of the FP64 residual partial sums, never
+ * the fields. */
+int rbf_set_persistent_block(rbf_ctx *ctx, int block);
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
@@ -252,6 +280,9 @@ int rbf_batch_init(rbf_batch *b, const rbf_params *p);
  * when every cell converged, RBF_ENOTCONVERGED otherwise (res filled),
  * RBF_ETIMEOUT if a grid barrier of the persistent kernel timed out. */
 int rbf_batch_solve(rbf_batch *b, const rbf_solve_opts *opts, rbf_batch_cell_result *res);
+/* rbf_autotune_persistent over all cells of the batch in one launch per trial
+ * (the choice applies to every cell). */
+int rbf_batch_autotune(rbf_batch *b, int trial_steps, rbf_tune_report *rep);
 int rbf_batch_num_cells(const rbf_batch *b);
 rbf_ctx *rbf_batch_cell(rbf_batch *b, int cell);
 
@@ -290,10 +321,12 @@ int rbf_mlp_train(rbf_mlp *mlp, int steps, int batch, double lr, uint64_t seed, 
 int rbf_mlp_gradient(rbf_mlp *mlp, int batch, const int64_t *sample_idx, float *grad, double *loss);
 /* Network output for n points: out (n x 4) in the scaled units of the targets. */
 int rbf_mlp_predict(rbf_mlp *mlp, int64_t n, const double *xyz, const float *radius, const float *sdf, float *out);
-/* Warm start: write scale x the prediction at the context's nodes into its ACM
- * fields (velocity zero on wall nodes) and recompute C of Eq. MNS_C.  The context
- * must be an initialised ACM context with a sphere, on the same device. */
-int rbf_mlp_warm_start(rbf_mlp *mlp, rbf_ctx *ctx, double scale);
+/* Warm start: write scale[c] x output c of the prediction at the context's nodes
+ * into its ACM fields (c = 0..3: u, v, w, p; velocity zero on wall nodes; the low
+ * words of an RBF_FP32C context zeroed) and recompute C of Eq. MNS_C.  The
+ * context must be an initialised ACM context with a sphere, on the same device.
+ * scale: 4 doubles (host). */
+int rbf_mlp_warm_start(rbf_mlp *mlp, rbf_ctx *ctx, const double *scale);
 int64_t rbf_mlp_launch_count(const rbf_mlp *mlp);
 
 /* Permeability exactly as rbf_permeability(m_p), for callers that cannot allocate

@@ -25,7 +25,7 @@ from . import _build
 RBF_OK, RBF_EINVAL, RBF_ECUDA, RBF_ESINGULAR = 0, -1, -2, -3
 RBF_EDIVERGED, RBF_ENOTCONVERGED, RBF_ETIMEOUT, RBF_ENOMEM = -4, -5, -6, -7
 RBF_SOLVER_ACM, RBF_SOLVER_LBM = 0, 1
-RBF_FP64, RBF_FP32 = 0, 1
+RBF_FP64, RBF_FP32, RBF_FP32C = 0, 1, 2
 RBF_OP_DX, RBF_OP_DY, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_LBM0 = 0, 1, 2, 3, 16
 
 _ERRNAMES = {RBF_EINVAL: "EINVAL", RBF_ECUDA: "ECUDA", RBF_ESINGULAR: "ESINGULAR",
@@ -100,6 +100,9 @@ ABI = {
     "rbf_set_kernel_variant": (_I, [_P, _I]),
     "rbf_permeability_static": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rbf_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
+    "rbf_autotune_persistent": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
+    "rbf_set_persistent_block": (_I, [_P, _I]),
+    "rbf_batch_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
     "rbf_batch_create": (_I, [ctypes.POINTER(_P), _I, _P]),
     "rbf_batch_destroy": (_I, [_P]),
     "rbf_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -119,7 +122,7 @@ ABI = {
     "rbf_mlp_train": (_I, [_P, _I, _I, _D, ctypes.c_uint64, _P]),
     "rbf_mlp_gradient": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
     "rbf_mlp_predict": (_I, [_P, _I64, _P, _P, _P, _P]),
-    "rbf_mlp_warm_start": (_I, [_P, _P, _D]),
+    "rbf_mlp_warm_start": (_I, [_P, _P, _P]),
     "rbf_mlp_launch_count": (_I64, [_P]),
 }
 
@@ -304,7 +307,9 @@ class Solver:
 
     def set_kernel_variant(self, variant: int):
         """LBM step schedule: 0 / 2 one node per thread (256 / 128 threads per
-        block); 1 / 3 / 4 / 5 one population pair per warp, unrolled 5 / 3 / 6 / 2."""
+        block); 1 / 3 / 4 / 5 one population pair per warp, unrolled 5 / 3 / 6 / 2;
+        6 / 7 one node per thread on the node-record layout (256 threads; 128
+        threads unrolled 2).  The state is rewritten when the layout changes."""
         self._ck(self._L.rbf_set_kernel_variant(self._h, int(variant)))
 
     def autotune(self, trial_steps: int = 50):
@@ -312,6 +317,18 @@ class Solver:
         the state is restored afterwards.  Returns {code: ms_per_step}, chosen."""
         r = rbf_tune_report()
         self._ck(self._L.rbf_autotune(self._h, int(trial_steps), ctypes.byref(r)))
+        return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
+
+    def set_persistent_block(self, block: int):
+        """Threads per block of the persistent ACM driver (32, 64, 128, 256)."""
+        self._ck(self._L.rbf_set_persistent_block(self._h, int(block)))
+
+    def autotune_persistent(self, trial_steps: int = 200):
+        """ACM: time the persistent driver's block sizes on this case and keep the
+        fastest for solve(); the state is restored afterwards.  Returns
+        {threads per block: ms_per_step}, chosen."""
+        r = rbf_tune_report()
+        self._ck(self._L.rbf_autotune_persistent(self._h, int(trial_steps), ctypes.byref(r)))
         return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
 
     def launch_count(self) -> int:
@@ -396,6 +413,17 @@ class Batch:
         self._ck(self._L.rbf_batch_solve(self._h, ctypes.byref(o), res), ok=(RBF_OK, RBF_ENOTCONVERGED))
         return [dict(steps=r.steps, residual=r.residual, k_over_d2=r.k_over_d2, status=r.status) for r in res]
 
+    def set_persistent_block(self, block: int):
+        for i in range(len(self._cells)):
+            self.cell(i).set_persistent_block(block)
+
+    def autotune(self, trial_steps: int = 100):
+        """Time the persistent driver's block sizes over all cells and keep the
+        fastest; the cells' state is restored afterwards."""
+        r = rbf_tune_report()
+        self._ck(self._L.rbf_batch_autotune(self._h, int(trial_steps), ctypes.byref(r)))
+        return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
+
     def cell(self, i: int) -> Solver:
         h = self._L.rbf_batch_cell(self._h, i)
         if not h:
@@ -417,6 +445,7 @@ class Mlp:
             raise RbfError(rc, "rbf_mlp_create failed (no usable CUDA device?)")
         self._h = h
         self.n_params = int(L.rbf_mlp_num_params())
+        self.out_scale = np.ones(4)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -471,8 +500,12 @@ class Mlp:
         self._ck(self._L.rbf_mlp_predict(self._h, len(x), _ptr(x), _ptr(r), _ptr(s), _ptr(out)))
         return out
 
-    def warm_start(self, solver: "Solver", scale: float = 1.0):
-        self._ck(self._L.rbf_mlp_warm_start(self._h, solver._h, float(scale)))
+    def warm_start(self, solver: "Solver", scale=1.0):
+        """Write the prediction into the solver's fields: output c times
+        scale * out_scale[c] (out_scale: the per-output factor the targets were
+        divided by for training, ones by default)."""
+        sc = np.ascontiguousarray(np.broadcast_to(np.asarray(scale, np.float64), (4,)) * self.out_scale, np.float64)
+        self._ck(self._L.rbf_mlp_warm_start(self._h, solver._h, _ptr(sc)))
 
     def launch_count(self) -> int:
         return int(self._L.rbf_mlp_launch_count(self._h))

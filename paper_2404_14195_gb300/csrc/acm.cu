@@ -12,16 +12,24 @@
 // max |v| is reduced per block with warp shuffles and merged with one 64-bit
 // atomicMax per block into one of two ping-pong slots (non-negative IEEE values
 // order like their bit patterns), which the next pressure sweep reads.
+//
+// Compensated FP32 (CP = true): u, v, w, p and v' are carried as float pairs
+// hi + lo.  Gathers and all stencil arithmetic read the hi words only; every
+// update of a field adds its increment to the pair with comp_add, so the slow
+// late-time changes of a near-steady field, far below one float ulp of the
+// field, are not rounded away (the explicit update otherwise stalls short of
+// the steady state).  Wall values are exact zeros in both words.
 #include "acm.cuh"
 
 namespace rbf {
 
-template <typename T>
+template <typename T, bool CP>
 __global__ void __launch_bounds__(256) k_acm_predict(AcmArgs<T> a) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     if (a.type[i]) {
         a.us[i] = (T)0; a.vs[i] = (T)0; a.ws[i] = (T)0;
+        if constexpr (CP) { a.usl[i] = (T)0; a.vsl[i] = (T)0; a.wsl[i] = (T)0; }
         return;
     }
     const int64_t s = i >> 5;
@@ -44,9 +52,21 @@ __global__ void __launch_bounds__(256) k_acm_predict(AcmArgs<T> a) {
     T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
     T adv_v = ui * gv[0] + vi * gv[1] + wi * gv[2];
     T adv_w = ui * gw[0] + vi * gw[1] + wi * gw[2];
-    a.us[i] = ui + a.dt * (a.nu * gu[3] - adv_u + a.gx);
-    a.vs[i] = vi + a.dt * (a.nu * gv[3] - adv_v + a.gy);
-    a.ws[i] = wi + a.dt * (a.nu * gw[3] - adv_w + a.gz);
+    if constexpr (CP) {
+        T h = ui, l = a.ul[i];
+        comp_add(h, l, a.dt * (a.nu * gu[3] - adv_u + a.gx));
+        a.us[i] = h; a.usl[i] = l;
+        h = vi; l = a.vl[i];
+        comp_add(h, l, a.dt * (a.nu * gv[3] - adv_v + a.gy));
+        a.vs[i] = h; a.vsl[i] = l;
+        h = wi; l = a.wl[i];
+        comp_add(h, l, a.dt * (a.nu * gw[3] - adv_w + a.gz));
+        a.ws[i] = h; a.wsl[i] = l;
+    } else {
+        a.us[i] = ui + a.dt * (a.nu * gu[3] - adv_u + a.gx);
+        a.vs[i] = vi + a.dt * (a.nu * gv[3] - adv_v + a.gy);
+        a.ws[i] = wi + a.dt * (a.nu * gw[3] - adv_w + a.gz);
+    }
 }
 
 // speed of sound of Eq. MNS_C from the max |v| stored (as double bits) in a slot
@@ -55,7 +75,7 @@ __device__ __forceinline__ double acm_C(const unsigned long long *slot, double b
     return beta * (vmax > vref ? vmax : vref);
 }
 
-template <typename T>
+template <typename T, bool CP>
 __global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__restrict__ u, const T *__restrict__ v,
                                                      const T *__restrict__ w, int read_slot, int zero_slot) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -75,12 +95,18 @@ __global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__r
         div += wx * u[q] + wy * v[q] + wz * w[q];
     }
     const T Ct = (T)C;
-    a.p[i] = a.p[i] - a.dt * Ct * Ct * a.rho * div;
+    if constexpr (CP) {
+        T h = a.p[i], l = a.pl[i];
+        comp_add(h, l, -(a.dt * Ct * Ct * a.rho * div));
+        a.p[i] = h; a.pl[i] = l;
+    } else {
+        a.p[i] = a.p[i] - a.dt * Ct * Ct * a.rho * div;
+    }
 }
 
 // wall pressure from the Neumann condition, on the wall nodes' own stencils
 // {b, nearest fluid nodes}: p_b = -sum_{j>=1} w^n_j p_j / w^n_0
-template <typename T>
+template <typename T, bool CP>
 __global__ void __launch_bounds__(256) k_acm_wall_pressure(AcmArgs<T> a) {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= a.nb) return;
@@ -92,10 +118,12 @@ __global__ void __launch_bounds__(256) k_acm_wall_pressure(AcmArgs<T> a) {
     T acc = 0;
 #pragma unroll 4
     for (int j = 1; j < n_l; ++j) acc += __ldg(wp + (j << 5)) * a.p[__ldg(ip + (j << 5))];
-    a.p[a.wall[b]] = -acc / __ldg(wp);
+    const int32_t wb = a.wall[b];
+    a.p[wb] = -acc / __ldg(wp);
+    if constexpr (CP) a.pl[wb] = (T)0;
 }
 
-template <typename T>
+template <typename T, bool CP>
 __global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slot) {
     __shared__ double red[8];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -103,6 +131,7 @@ __global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slo
     if (i < a.n) {
         if (a.type[i]) {
             a.u[i] = (T)0; a.v[i] = (T)0; a.w_[i] = (T)0;
+            if constexpr (CP) { a.ul[i] = (T)0; a.vl[i] = (T)0; a.wl[i] = (T)0; }
         } else {
             const int64_t s = i >> 5;
             const int lane = (int)(i & 31);
@@ -110,15 +139,25 @@ __global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slo
             const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
             const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
             T gx = 0, gy = 0, gz = 0;
-        #pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
+#pragma unroll 5
+            for (int j = 0; j < n_l; ++j) {
                 T pq = a.p[__ldg(ip + (j << 5))];
                 gx += __ldg(wp + (j << 5)) * pq;
                 gy += __ldg(wp + ((n_l + j) << 5)) * pq;
                 gz += __ldg(wp + ((2 * n_l + j) << 5)) * pq;
             }
             const T f = a.dt / a.rho;
-            T un = a.us[i] - f * gx, vn = a.vs[i] - f * gy, wn = a.ws[i] - f * gz;
+            T un, vn, wn;
+            if constexpr (CP) {
+                T l = a.usl[i];
+                un = a.us[i]; comp_add(un, l, -(f * gx)); a.ul[i] = l;
+                l = a.vsl[i];
+                vn = a.vs[i]; comp_add(vn, l, -(f * gy)); a.vl[i] = l;
+                l = a.wsl[i];
+                wn = a.ws[i]; comp_add(wn, l, -(f * gz)); a.wl[i] = l;
+            } else {
+                un = a.us[i] - f * gx; vn = a.vs[i] - f * gy; wn = a.ws[i] - f * gz;
+            }
             a.u[i] = un; a.v[i] = vn; a.w_[i] = wn;
             speed = (double)sqrt(un * un + vn * vn + wn * wn);
         }
@@ -146,14 +185,13 @@ __global__ void k_acm_vmax(AcmArgs<T> a, int slot) {
 // Iteration g of the run (counted over all steps) writes max |v| into slot g % 2;
 // the pressure sweep of iteration g reads slot (g + 1) % 2 (the previous
 // iteration's) and clears slot g % 2 for its own correction sweep.
-template <typename T>
-cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                            LaunchRecorder *rec, int block) {
-    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+template <typename T, bool CP>
+cudaError_t acm_launch_step_cp(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
+                               LaunchRecorder *rec, int block) {
     const unsigned gb = (unsigned)((a.n + block - 1) / block);
     const unsigned gw = (unsigned)((a.nb + 255) / 256);
     if (rec) rec->begin(st, 0);
-    k_acm_predict<T><<<gb, block, 0, st>>>(a);
+    k_acm_predict<T, CP><<<gb, block, 0, st>>>(a);
     if (rec) rec->end(st);
     ++*launches;
     for (int it = 0; it < n_p; ++it) {
@@ -162,21 +200,32 @@ cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream
         const T *w = it == 0 ? a.ws : a.w_;
         const int g = (parity + it) & 1;
         if (rec) rec->begin(st, 1);
-        k_acm_pressure<T><<<gb, block, 0, st>>>(a, u, v, w, g ^ 1, g);
+        k_acm_pressure<T, CP><<<gb, block, 0, st>>>(a, u, v, w, g ^ 1, g);
         if (rec) rec->end(st);
         ++*launches;
         if (a.nb > 0) {
             if (rec) rec->begin(st, 2);
-            k_acm_wall_pressure<T><<<gw, 256, 0, st>>>(a);
+            k_acm_wall_pressure<T, CP><<<gw, 256, 0, st>>>(a);
             if (rec) rec->end(st);
             ++*launches;
         }
         if (rec) rec->begin(st, 3);
-        k_acm_correct<T><<<gb, block, 0, st>>>(a, g);
+        k_acm_correct<T, CP><<<gb, block, 0, st>>>(a, g);
         if (rec) rec->end(st);
         ++*launches;
     }
     return cudaGetLastError();
+}
+
+// the compensated kernels run when the low words are present
+template <typename T>
+cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
+                            LaunchRecorder *rec, int block) {
+    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+    const bool cp = a.ul && a.vl && a.wl && a.pl && a.usl && a.vsl && a.wsl;
+    if (!cp && (a.ul || a.vl || a.wl || a.pl || a.usl || a.vsl || a.wsl)) return cudaErrorInvalidValue;
+    return cp ? acm_launch_step_cp<T, true>(a, n_p, parity, st, launches, rec, block)
+              : acm_launch_step_cp<T, false>(a, n_p, parity, st, launches, rec, block);
 }
 
 template <typename T>
@@ -189,7 +238,11 @@ cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st) {
 
 template <typename T>
 cudaError_t acm_launch_predict_only(const AcmArgs<T> &a, cudaStream_t st) {
-    k_acm_predict<T><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+    if (a.ul) {
+        k_acm_predict<T, true><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    k_acm_predict<T, false><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -16,10 +16,32 @@ struct AcmArgs {
     const T *wn;          // SELL over wall nodes: normal-derivative weights
     T *u, *v, *w_, *p;    // velocity and pressure
     T *us, *vs, *ws;      // intermediate velocity v'
+    // compensated state (null unless the context runs RBF_FP32C): low words of
+    // u, v, w, p, u', v', w'; a field's value is then hi + lo
+    T *ul, *vl, *wl, *pl, *usl, *vsl, *wsl;
     unsigned long long *vmax;  // 2 ping-pong slots of max |v| (double bits)
     T dt, nu, gx, gy, gz, rho;
     double beta, vref;
 };
+
+// (hi, lo) += d for a value carried as the unevaluated sum hi + lo.  The rounding
+// error of hi + d (Knuth's TwoSum) joins lo and the pair is renormalised
+// (Dekker's Fast2Sum), so increments far below one ulp of hi still accumulate
+// instead of rounding away.  Explicit round-to-nearest adds keep the compiler
+// from contracting them with the product that formed d.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ void comp_add(T &hi, T &lo, T d) {
+    const T s = add_rn(hi, d);
+    const T bb = sub_rn(s, hi);
+    const T err = add_rn(sub_rn(hi, sub_rn(s, bb)), sub_rn(d, bb));
+    const T l = add_rn(lo, err);
+    hi = add_rn(s, l);
+    lo = sub_rn(l, sub_rn(hi, s));
+}
 
 template <typename T>
 cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,

@@ -15,7 +15,12 @@
 // after a wall-clock limit, raise an error flag and leave the loop, so a launch
 // whose blocks are not co-resident ends with RBF_ETIMEOUT instead of hanging.
 // The cooperative launch itself guarantees co-residency.
+//
+// CP = true is the compensated FP32 state of acm.cu (hi + lo pairs, comp_add
+// updates, gathers of the hi words); its residual differences include the low
+// words.
 #include "acm_persist.cuh"
+#include "acm.cuh"
 #include "tc.cuh"
 
 namespace rbf {
@@ -59,13 +64,20 @@ __device__ __forceinline__ double slot_C(const unsigned long long *slot, double 
     return beta * (vmax > vref ? vmax : vref);
 }
 
-template <typename T>
+template <typename T, bool CP>
 __device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool snapshot) {
     const int64_t i = (ls << 5) + lane;
     if (i >= c.n) return;
     const T ui = c.u[i], vi = c.v[i], wi = c.w_[i];
-    if (snapshot) { c.uo[i] = ui; c.vo[i] = vi; c.wo[i] = wi; }
-    if (c.type[i]) { c.us[i] = (T)0; c.vs[i] = (T)0; c.ws[i] = (T)0; return; }
+    if (snapshot) {
+        c.uo[i] = ui; c.vo[i] = vi; c.wo[i] = wi;
+        if constexpr (CP) { c.uol[i] = c.ul[i]; c.vol[i] = c.vl[i]; c.wol[i] = c.wl[i]; }
+    }
+    if (c.type[i]) {
+        c.us[i] = (T)0; c.vs[i] = (T)0; c.ws[i] = (T)0;
+        if constexpr (CP) { c.usl[i] = (T)0; c.vsl[i] = (T)0; c.wsl[i] = (T)0; }
+        return;
+    }
     const int n_l = c.n_l;
     const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
@@ -82,12 +94,24 @@ __device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool s
     const T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
     const T adv_v = ui * gv[0] + vi * gv[1] + wi * gv[2];
     const T adv_w = ui * gw[0] + vi * gw[1] + wi * gw[2];
-    c.us[i] = ui + c.dt * (c.nu * gu[3] - adv_u + c.gx);
-    c.vs[i] = vi + c.dt * (c.nu * gv[3] - adv_v + c.gy);
-    c.ws[i] = wi + c.dt * (c.nu * gw[3] - adv_w + c.gz);
+    if constexpr (CP) {
+        T h = ui, l = c.ul[i];
+        comp_add(h, l, c.dt * (c.nu * gu[3] - adv_u + c.gx));
+        c.us[i] = h; c.usl[i] = l;
+        h = vi; l = c.vl[i];
+        comp_add(h, l, c.dt * (c.nu * gv[3] - adv_v + c.gy));
+        c.vs[i] = h; c.vsl[i] = l;
+        h = wi; l = c.wl[i];
+        comp_add(h, l, c.dt * (c.nu * gw[3] - adv_w + c.gz));
+        c.ws[i] = h; c.wsl[i] = l;
+    } else {
+        c.us[i] = ui + c.dt * (c.nu * gu[3] - adv_u + c.gx);
+        c.vs[i] = vi + c.dt * (c.nu * gv[3] - adv_v + c.gy);
+        c.ws[i] = wi + c.dt * (c.nu * gw[3] - adv_w + c.gz);
+    }
 }
 
-template <typename T>
+template <typename T, bool CP>
 __device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool first, int g) {
     const int64_t i = (ls << 5) + lane;
     if (i >= c.n || c.type[i]) return;
@@ -105,10 +129,16 @@ __device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool 
         div += wp[j << 5] * u[q] + wp[(n_l + j) << 5] * v[q] + wp[(2 * n_l + j) << 5] * w[q];
     }
     const T Ct = (T)C;
-    c.p[i] = c.p[i] - c.dt * Ct * Ct * c.rho * div;
+    if constexpr (CP) {
+        T h = c.p[i], l = c.pl[i];
+        comp_add(h, l, -(c.dt * Ct * Ct * c.rho * div));
+        c.p[i] = h; c.pl[i] = l;
+    } else {
+        c.p[i] = c.p[i] - c.dt * Ct * Ct * c.rho * div;
+    }
 }
 
-template <typename T>
+template <typename T, bool CP>
 __device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
     const int64_t b = (ls << 5) + lane;
     if (b >= c.nb) return;
@@ -118,14 +148,20 @@ __device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
     T acc = 0;
 #pragma unroll 4
     for (int j = 1; j < n_l; ++j) acc += wp[j << 5] * c.p[ip[j << 5]];
-    c.p[c.wall[b]] = -acc / wp[0];
+    const int32_t wb = c.wall[b];
+    c.p[wb] = -acc / wp[0];
+    if constexpr (CP) c.pl[wb] = (T)0;
 }
 
-template <typename T>
+template <typename T, bool CP>
 __device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
     const int64_t i = (ls << 5) + lane;
     if (i >= c.n) return 0.0;
-    if (c.type[i]) { c.u[i] = (T)0; c.v[i] = (T)0; c.w_[i] = (T)0; return 0.0; }
+    if (c.type[i]) {
+        c.u[i] = (T)0; c.v[i] = (T)0; c.w_[i] = (T)0;
+        if constexpr (CP) { c.ul[i] = (T)0; c.vl[i] = (T)0; c.wl[i] = (T)0; }
+        return 0.0;
+    }
     const int n_l = c.n_l;
     const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
     const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
@@ -138,12 +174,22 @@ __device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
         gz += wp[(2 * n_l + j) << 5] * pq;
     }
     const T f = c.dt / c.rho;
-    const T un = c.us[i] - f * gx, vn = c.vs[i] - f * gy, wn = c.ws[i] - f * gz;
+    T un, vn, wn;
+    if constexpr (CP) {
+        T l = c.usl[i];
+        un = c.us[i]; comp_add(un, l, -(f * gx)); c.ul[i] = l;
+        l = c.vsl[i];
+        vn = c.vs[i]; comp_add(vn, l, -(f * gy)); c.vl[i] = l;
+        l = c.wsl[i];
+        wn = c.ws[i]; comp_add(wn, l, -(f * gz)); c.wl[i] = l;
+    } else {
+        un = c.us[i] - f * gx; vn = c.vs[i] - f * gy; wn = c.ws[i] - f * gz;
+    }
     c.u[i] = un; c.v[i] = vn; c.w_[i] = wn;
     return (double)sqrt(un * un + vn * vn + wn * wn);
 }
 
-template <typename T>
+template <typename T, bool CP>
 __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__restrict__ cells, PersistCtl ctl) {
     __shared__ double racc[PERSIST_MAX_CELLS][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -160,35 +206,37 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
         for (int64_t s = w0; s < ctl.nslices; s += wstride) {
             const int2 sl = ctl.slices[s];
             if (ctl.done[sl.x]) continue;
-            phase_predict<T>(cells[sl.x], sl.y, lane, check);
+            phase_predict<T, CP>(cells[sl.x], sl.y, lane, check);
         }
         if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
         bool broke = false;
         for (int it = 0; it < ctl.n_p && !broke; ++it) {
             // slot parity of iteration `it` of this step for each cell: (parity0 + n_p * step + it) & 1
-            if (blockIdx.x == 0 && threadIdx.x < ctl.ncells && !ctl.done[threadIdx.x]) {
-                const CellDesc<T> &c = cells[threadIdx.x];
-                const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
-                c.vmax[g] = 0ULL;
-            }
+            if (blockIdx.x == 0)
+                for (int ci = threadIdx.x; ci < ctl.ncells; ci += blockDim.x) {
+                    if (ctl.done[ci]) continue;
+                    const CellDesc<T> &c = cells[ci];
+                    const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
+                    c.vmax[g] = 0ULL;
+                }
             for (int64_t s = w0; s < ctl.nslices; s += wstride) {
                 const int2 sl = ctl.slices[s];
                 if (ctl.done[sl.x]) continue;
                 const CellDesc<T> &c = cells[sl.x];
-                phase_pressure<T>(c, sl.y, lane, it == 0, (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1));
+                phase_pressure<T, CP>(c, sl.y, lane, it == 0, (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1));
             }
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
             for (int64_t s = w0; s < ctl.nwslices; s += wstride) {
                 const int2 sl = ctl.wslices[s];
                 if (ctl.done[sl.x]) continue;
-                phase_wall<T>(cells[sl.x], sl.y, lane);
+                phase_wall<T, CP>(cells[sl.x], sl.y, lane);
             }
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
             for (int64_t s = w0; s < ctl.nslices; s += wstride) {
                 const int2 sl = ctl.slices[s];
                 if (ctl.done[sl.x]) continue;
                 const CellDesc<T> &c = cells[sl.x];
-                double sp = phase_correct<T>(c, sl.y, lane);
+                double sp = phase_correct<T, CP>(c, sl.y, lane);
                 for (int off = 16; off > 0; off >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, off));
                 if (lane == 0 && sp > 0.0) {
                     const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
@@ -208,10 +256,17 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
                 const int64_t i = ((int64_t)sl.y << 5) + lane;
                 double d2 = 0.0, v2 = 0.0;
                 if (i < c.n && !c.type[i]) {
-                    const double a = (double)c.u[i] - (double)c.uo[i], b = (double)c.v[i] - (double)c.vo[i];
-                    const double e = (double)c.w_[i] - (double)c.wo[i];
+                    double a = (double)c.u[i] - (double)c.uo[i], b = (double)c.v[i] - (double)c.vo[i];
+                    double e = (double)c.w_[i] - (double)c.wo[i];
+                    double uu = c.u[i], vv = c.v[i], ww = c.w_[i];
+                    if constexpr (CP) {
+                        a += (double)c.ul[i] - (double)c.uol[i];
+                        b += (double)c.vl[i] - (double)c.vol[i];
+                        e += (double)c.wl[i] - (double)c.wol[i];
+                        uu += c.ul[i]; vv += c.vl[i]; ww += c.wl[i];
+                    }
                     d2 = a * a + b * b + e * e;
-                    v2 = (double)c.u[i] * c.u[i] + (double)c.v[i] * c.v[i] + (double)c.w_[i] * c.w_[i];
+                    v2 = uu * uu + vv * vv + ww * ww;
                 }
                 for (int off = 16; off > 0; off >>= 1) {
                     d2 += __shfl_xor_sync(0xffffffffu, d2, off);
@@ -226,9 +281,9 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
             for (int t = threadIdx.x; t < 2 * ctl.ncells; t += blockDim.x)
                 ctl.partial[(int64_t)blockIdx.x * 2 * PERSIST_MAX_CELLS + t] = racc[t >> 1][t & 1];
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
-            if (blockIdx.x == 0 && threadIdx.x < ctl.ncells) {
-                const int c = threadIdx.x;
-                if (!ctl.done[c]) {
+            if (blockIdx.x == 0) {
+                for (int c = threadIdx.x; c < ctl.ncells; c += blockDim.x) {
+                    if (ctl.done[c]) continue;
                     double d2 = 0.0, v2 = 0.0;
                     for (unsigned b = 0; b < nblocks; ++b) {
                         d2 += ctl.partial[(int64_t)b * 2 * PERSIST_MAX_CELLS + 2 * c];
@@ -237,38 +292,47 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
                     const double res = v2 > 0.0 ? sqrt(d2) / sqrt(v2) : 0.0;
                     ctl.resid[c] = res;
                     ctl.steps[c] = step + 1;
-                    if (!isfinite(res)) { ctl.done[c] = 3; }
+                    if (!isfinite(res)) ctl.done[c] = 3;
                     else if (v2 > 0.0 && res < ctl.tol) ctl.done[c] = 1;
                 }
             }
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
-        } else if (blockIdx.x == 0 && threadIdx.x < ctl.ncells && !ctl.done[threadIdx.x]) {
-            ctl.steps[threadIdx.x] = step + 1;
+        } else if (blockIdx.x == 0) {
+            for (int c = threadIdx.x; c < ctl.ncells; c += blockDim.x)
+                if (!ctl.done[c]) ctl.steps[c] = step + 1;
         }
     }
 }
 
 }  // namespace
 
+bool persist_block_ok(int block) { return block == 32 || block == 64 || block == 128 || block == 256; }
+
 template <typename T>
-cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, cudaStream_t st) {
+cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, int block,
+                                  bool cp, cudaStream_t st) {
+    if (!persist_block_ok(block) || nblocks < 1) return cudaErrorInvalidValue;
     void *args[] = {(void *)&cells_dev, (void *)&ctl};
-    return cudaLaunchCooperativeKernel((const void *)k_acm_persistent<T>, dim3(nblocks), dim3(256), args, 0, st);
+    const void *fn = cp ? (const void *)k_acm_persistent<T, true> : (const void *)k_acm_persistent<T, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(block), args, 0, st);
 }
 
 template <typename T>
-cudaError_t acm_persistent_max_blocks(int *blocks) {
+cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp) {
+    if (!persist_block_ok(block)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T>, 256, 0);
+    if (e == cudaSuccess)
+        e = cp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, true>, block, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, false>, block, 0);
     *blocks = sms * per;
     return e;
 }
 
-template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const PersistCtl &, int, cudaStream_t);
-template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, cudaStream_t);
-template cudaError_t acm_persistent_max_blocks<float>(int *);
-template cudaError_t acm_persistent_max_blocks<double>(int *);
+template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const PersistCtl &, int, int, bool, cudaStream_t);
+template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, int, bool, cudaStream_t);
+template cudaError_t acm_persistent_max_blocks<float>(int *, int, bool);
+template cudaError_t acm_persistent_max_blocks<double>(int *, int, bool);
 
 }  // namespace rbf

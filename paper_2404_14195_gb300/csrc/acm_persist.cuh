@@ -21,6 +21,9 @@ struct CellDesc {
     T *u, *v, *w_, *p;
     T *us, *vs, *ws;
     T *uo, *vo, *wo;         // snapshot for the residual
+    // compensated state (RBF_FP32C, else null): low words of u, v, w, p, u', v',
+    // w' and of the snapshot
+    T *ul, *vl, *wl, *pl, *usl, *vsl, *wsl, *uol, *vol, *wol;
     unsigned long long *vmax;  // 2 slots
     T dt, nu, gx, gy, gz, rho;
     double beta, vref;
@@ -43,9 +46,12 @@ struct PersistCtl {
     int n_p;
 };
 
+// cp selects the compensated kernel (every cell then carries low words); block:
+// threads per block, 32, 64, 128 or 256 (one 32-node slice per warp at a time)
 template <typename T>
-cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, cudaStream_t st);
+cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, int block,
+                                  bool cp, cudaStream_t st);
 template <typename T>
-cudaError_t acm_persistent_max_blocks(int *blocks);
+cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp);
 
 }  // namespace rbf

@@ -50,10 +50,35 @@ struct DeviceGuard {
     }
 };
 
+// FP32 storage (plain or compensated)
+bool is_f32(const rbf_ctx *c) { return c->prec != RBF_FP64; }
+
+int persistent_solve(std::vector<rbf_ctx *> &cs, const rbf_solve_opts *o, std::vector<int64_t> &steps,
+                     std::vector<double> &resid, std::vector<int32_t> &done, std::string &err);
+
 void drop_graph(rbf_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
     ctx->gsteps = 0;
+}
+
+// Select an LBM schedule; an initialised state whose layout differs is rewritten
+// into the other population buffer, which becomes the current one.
+int switch_schedule(rbf_ctx *ctx, int variant) {
+    const int to = lbm_layout_of(variant);
+    if (ctx->inited && ctx->solver == RBF_SOLVER_LBM && to != ctx->lbm_layout) {
+        drop_graph(ctx);
+        const int c = ctx->cur;
+        if (ctx->prec == RBF_FP64)
+            CK(lbm_launch_relayout<double>(ctx->npad, ctx->q, ctx->lbm_layout, ctx->f64[c].p, to, ctx->f64[c ^ 1].p, ctx->st));
+        else
+            CK(lbm_launch_relayout<float>(ctx->npad, ctx->q, ctx->lbm_layout, ctx->f32[c].p, to, ctx->f32[c ^ 1].p, ctx->st));
+        ++ctx->launches;
+        ctx->cur = c ^ 1;
+    }
+    ctx->lbm_layout = to;
+    ctx->variant = variant;
+    return RBF_OK;
 }
 
 int binom(int a, int b) {
@@ -130,6 +155,13 @@ AcmArgs<T> acm_args(rbf_ctx *ctx, DevArr<T> *a, const DevArr<T> &ws, const DevAr
     g.idxb = ctx->idxb_sell.p; g.wn = wn.p;
     g.u = a[0].p; g.v = a[1].p; g.w_ = a[2].p; g.p = a[3].p;
     g.us = a[4].p; g.vs = a[5].p; g.ws = a[6].p;
+    g.ul = g.vl = g.wl = g.pl = g.usl = g.vsl = g.wsl = nullptr;
+    if constexpr (sizeof(T) == 4) {
+        if (ctx->prec == RBF_FP32C) {
+            DevArr<float> *l = ctx->l32;
+            g.ul = l[0].p; g.vl = l[1].p; g.wl = l[2].p; g.pl = l[3].p; g.usl = l[4].p; g.vsl = l[5].p; g.wsl = l[6].p;
+        }
+    }
     g.vmax = ctx->vmax.p;
     g.dt = (T)ctx->dt; g.nu = (T)ctx->prm.nu;
     g.gx = (T)ctx->prm.g[0]; g.gy = (T)ctx->prm.g[1]; g.gz = (T)ctx->prm.g[2];
@@ -140,7 +172,7 @@ AcmArgs<T> acm_args(rbf_ctx *ctx, DevArr<T> *a, const DevArr<T> &ws, const DevAr
 template <typename T>
 LbmArgs<T> lbm_args(rbf_ctx *ctx, DevArr<T> *f, const DevArr<T> &ws, int cur) {
     LbmArgs<T> g;
-    g.n = ctx->n; g.npad = ctx->npad; g.n_l = ctx->n_l;
+    g.n = ctx->n; g.npad = ctx->npad; g.n_l = ctx->n_l; g.layout = ctx->lbm_layout;
     g.idx = ctx->idx_sell.p; g.w = ws.p; g.mask = ctx->mask.p;
     g.fin = f[cur].p; g.fout = f[cur ^ 1].p;
     g.tp_inv = (T)(1.0 / ctx->tp); g.tm_inv = (T)(1.0 / ctx->tm);
@@ -154,12 +186,12 @@ cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
         if (ctx->solver == RBF_SOLVER_ACM) {
-            if (ctx->prec == RBF_FP32) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
+            if (is_f32(ctx)) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
             else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
             parity = (parity + ctx->n_p) & 1;
         } else {
             if (rec) rec->begin(ctx->st, 0);
-            if (ctx->prec == RBF_FP32) e = lbm_launch_step<float>(lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur), ctx->q, ctx->st, ctx->variant);
+            if (is_f32(ctx)) e = lbm_launch_step<float>(lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur), ctx->q, ctx->st, ctx->variant);
             else e = lbm_launch_step<double>(lbm_args<double>(ctx, ctx->f64, ctx->ws64, cur), ctx->q, ctx->st, ctx->variant);
             if (rec) rec->end(ctx->st);
             ++*launches;
@@ -547,7 +579,10 @@ int rbf_get_weights(rbf_ctx *ctx, int op, double *out) {
 int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
     if (!ctx || !p) return RBF_EINVAL;
     if (!ctx->weights_ok) return fail(ctx, RBF_EINVAL, "rbf_init: compute weights first");
-    if (p->precision != RBF_FP32 && p->precision != RBF_FP64) return fail(ctx, RBF_EINVAL, "rbf_init: bad precision");
+    if (p->precision != RBF_FP32 && p->precision != RBF_FP64 && p->precision != RBF_FP32C)
+        return fail(ctx, RBF_EINVAL, "rbf_init: bad precision");
+    if (p->precision == RBF_FP32C && ctx->solver != RBF_SOLVER_ACM)
+        return fail(ctx, RBF_EINVAL, "rbf_init: RBF_FP32C applies to the ACM solver only");
     if (!(p->nu > 0.0)) return fail(ctx, RBF_EINVAL, "rbf_init: nu must be > 0");
     DeviceGuard dg(ctx->device);
     CK(cudaStreamSynchronize(ctx->st));
@@ -559,6 +594,7 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
     const double gmag = std::sqrt(p->g[0] * p->g[0] + p->g[1] * p->g[1] + p->g[2] * p->g[2]);
     const int64_t n = ctx->n, npad = ctx->npad;
     for (auto &a : ctx->a32) a.release();
+    for (auto &a : ctx->l32) a.release();
     for (auto &a : ctx->a64) a.release();
     for (auto &a : ctx->f32) a.release();
     for (auto &a : ctx->f64) a.release();
@@ -570,8 +606,9 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
         ctx->n_p = p->n_p > 0 ? p->n_p : 3;
         ctx->parity = 0;
         for (int a = 0; a < 10; ++a) {
-            if (ctx->prec == RBF_FP32) { CK(ctx->a32[a].alloc(npad)); CK(ctx->a32[a].zero(ctx->st)); }
+            if (is_f32(ctx)) { CK(ctx->a32[a].alloc(npad)); CK(ctx->a32[a].zero(ctx->st)); }
             else { CK(ctx->a64[a].alloc(npad)); CK(ctx->a64[a].zero(ctx->st)); }
+            if (ctx->prec == RBF_FP32C) { CK(ctx->l32[a].alloc(npad)); CK(ctx->l32[a].zero(ctx->st)); }
         }
         CK(ctx->vmax.zero(ctx->st));  // v = 0: max |v| = 0, C = beta v_ref
     } else {
@@ -583,8 +620,9 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
         ctx->dt = ctx->lbm_dt;
         for (int a = 0; a < 3; ++a) ctx->gl[a] = p->g[a] * ctx->lbm_dt * ctx->lbm_dt / ctx->dx;
         ctx->cur = 0;
-        const int64_t sz = (int64_t)ctx->q * npad;
-        if (ctx->prec == RBF_FP32) {
+        ctx->lbm_layout = lbm_layout_of(ctx->variant);
+        const int64_t sz = (int64_t)lbm_rec_len(ctx->q) * npad;  // room for either layout
+        if (is_f32(ctx)) {
             CK(ctx->f32[0].alloc(sz)); CK(ctx->f32[1].alloc(sz)); CK(ctx->f32[1].zero(ctx->st));
             LbmArgs<float> a = lbm_args<float>(ctx, ctx->f32, ctx->ws32, 1);  // writes f32[0]
             CK(lbm_launch_init<float>(a, ctx->q, ctx->st));
@@ -636,8 +674,9 @@ int rbf_set_kernel_variant(rbf_ctx *ctx, int variant) {
     if (!ctx) return RBF_EINVAL;
     if (variant < 0 || variant >= LBM_N_SCHEDULES)
         return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: schedule code out of range");
-    ctx->variant = variant;
-    return RBF_OK;
+    DeviceGuard dg(ctx->device);
+    const int rc = switch_schedule(ctx, variant);
+    return rc;
 }
 
 namespace {
@@ -659,6 +698,7 @@ int save_state(rbf_ctx *ctx, StateCopy &sc) {
     };
     for (int i = 0; i < 10; ++i) {
         CK(add(ctx->a32[i].p, ctx->a32[i].n * sizeof(float)));
+        CK(add(ctx->l32[i].p, ctx->l32[i].n * sizeof(float)));
         CK(add(ctx->a64[i].p, ctx->a64[i].n * sizeof(double)));
     }
     for (int i = 0; i < 2; ++i) {
@@ -682,14 +722,22 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     if (trial_steps < 2 || trial_steps > 2000) return fail(ctx, RBF_EINVAL, "rbf_autotune: 2 <= trial_steps <= 2000");
     DeviceGuard dg(ctx->device);
     drop_graph(ctx);
-    const int par0 = ctx->parity, cur0 = ctx->cur, var0 = ctx->variant, blk0 = ctx->acm_block;
+    const int par0 = ctx->parity, cur0 = ctx->cur, lay0 = ctx->lbm_layout;
     StateCopy sc;
     int rc = save_state(ctx, sc);
     if (rc) return rc;
+    // back to the saved state: buffers, current buffer, layout
+    auto back = [&]() -> int {
+        const int r = restore_state(ctx, sc);
+        ctx->parity = par0;
+        ctx->cur = cur0;
+        ctx->lbm_layout = lay0;
+        return r;
+    };
     std::vector<int> cands;
     if (ctx->solver == RBF_SOLVER_LBM)
         cands = {LBM_PAIR_PER_WARP, LBM_NODE_PER_THREAD, LBM_NODE_PER_THREAD_128, LBM_PAIR_PER_WARP_U3,
-                 LBM_PAIR_PER_WARP_U6, LBM_PAIR_PER_WARP_U2};
+                 LBM_PAIR_PER_WARP_U6, LBM_PAIR_PER_WARP_U2, LBM_RECORD_PER_THREAD, LBM_RECORD_PER_THREAD_128_U2};
     else
         cands = {256, 128, 64};
     rbf_tune_report r;
@@ -697,7 +745,12 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     double best = 1e300;
     int best_code = cands[0];
     for (size_t c = 0; c < cands.size() && c < 8; ++c) {
-        if (ctx->solver == RBF_SOLVER_LBM) ctx->variant = cands[c]; else ctx->acm_block = cands[c];
+        if (ctx->solver == RBF_SOLVER_LBM) {
+            rc = switch_schedule(ctx, cands[c]);
+            if (rc) return rc;
+        } else {
+            ctx->acm_block = cands[c];
+        }
         int64_t kl = 0;
         int par = ctx->parity, cu = ctx->cur;
         cudaError_t e = enqueue_steps(ctx, 2, par, cu, &kl);  // warm-up
@@ -715,17 +768,95 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
         r.ms_per_step[c] = per;
         r.n_candidates = (int)c + 1;
         if (per < best) { best = per; best_code = cands[c]; }
-        rc = restore_state(ctx, sc);
+        rc = back();
         if (rc) return rc;
     }
-    ctx->parity = par0;
-    ctx->cur = cur0;
-    (void)var0; (void)blk0;
-    if (ctx->solver == RBF_SOLVER_LBM) ctx->variant = best_code; else ctx->acm_block = best_code;
+    if (ctx->solver == RBF_SOLVER_LBM) {
+        rc = switch_schedule(ctx, best_code);
+        if (rc) return rc;
+    } else {
+        ctx->acm_block = best_code;
+    }
     r.chosen = best_code;
     r.solver = ctx->solver;
     if (rep) *rep = r;
     return RBF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Time the persistent driver over `cs` for every block size and keep the fastest
+// in every cell; the cells' fields and parities are restored after each trial.
+int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report *rep, std::string &err) {
+    rbf_ctx *ctx = cs[0];
+    std::vector<StateCopy> sc(cs.size());
+    std::vector<int> par0(cs.size());
+    for (size_t c = 0; c < cs.size(); ++c) {
+        drop_graph(cs[c]);
+        par0[c] = cs[c]->parity;
+        int rc = save_state(cs[c], sc[c]);
+        if (rc) { err = cs[c]->err; return rc; }
+    }
+    const int cands[4] = {256, 128, 64, 32};
+    rbf_tune_report r;
+    std::memset(&r, 0, sizeof(r));
+    double best = 1e300;
+    int best_code = cands[0];
+    rbf_solve_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.tol = 1e-300;
+    std::vector<int64_t> st;
+    std::vector<double> rs;
+    std::vector<int32_t> dn;
+    for (int k = 0; k < 4; ++k) {
+        for (rbf_ctx *x : cs) x->persist_block = cands[k];
+        double ms = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {  // warm-up, then the timed trial
+            o.max_steps = pass ? trial_steps : 2;
+            o.check_every = (int)o.max_steps;
+            const int rc = persistent_solve(cs, &o, st, rs, dn, err);
+            if (rc) return rc;
+            ms = ctx->persist_ms;
+        }
+        for (size_t c = 0; c < cs.size(); ++c) {
+            cs[c]->parity = par0[c];
+            const int rc = restore_state(cs[c], sc[c]);
+            if (rc) { err = cs[c]->err; return rc; }
+        }
+        r.code[k] = cands[k];
+        r.ms_per_step[k] = ms / trial_steps;
+        r.n_candidates = k + 1;
+        if (r.ms_per_step[k] < best) { best = r.ms_per_step[k]; best_code = cands[k]; }
+    }
+    for (rbf_ctx *x : cs) x->persist_block = best_code;
+    r.chosen = best_code;
+    r.solver = RBF_SOLVER_ACM;
+    if (rep) *rep = r;
+    return RBF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rbf_set_persistent_block(rbf_ctx *ctx, int block) {
+    if (!ctx) return RBF_EINVAL;
+    if (block != 32 && block != 64 && block != 128 && block != 256)
+        return fail(ctx, RBF_EINVAL, "rbf_set_persistent_block: block must be 32, 64, 128 or 256");
+    ctx->persist_block = block;
+    return RBF_OK;
+}
+
+int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
+    if (!ctx) return RBF_EINVAL;
+    if (!ctx->inited || ctx->solver != RBF_SOLVER_ACM)
+        return fail(ctx, RBF_EINVAL, "rbf_autotune_persistent: needs an initialised ACM context");
+    if (trial_steps < 2 || trial_steps > 20000) return fail(ctx, RBF_EINVAL, "rbf_autotune_persistent: 2 <= trial_steps <= 20000");
+    DeviceGuard dg(ctx->device);
+    std::vector<rbf_ctx *> cs{ctx};
+    std::string msg;
+    const int rc = tune_persistent(cs, trial_steps, rep, msg);
+    return rc ? fail(ctx, rc, msg.empty() ? std::string("rbf_autotune_persistent failed") : msg) : RBF_OK;
 }
 
 int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classes) {
@@ -770,12 +901,13 @@ int rbf_get_fields(rbf_ctx *ctx, double *uvwp) {
     DeviceGuard dg(ctx->device);
     DevArr<double> &out = ctx->stage;
     if (ctx->solver == RBF_SOLVER_ACM) {
-        if (ctx->prec == RBF_FP32) CK(launch_acm_export<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, out.p, ctx->st));
+        if (ctx->prec == RBF_FP32C) CK(launch_acm_export_pair(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, ctx->l32[0].p, ctx->l32[1].p, ctx->l32[2].p, ctx->l32[3].p, out.p, ctx->st));
+        else if (is_f32(ctx)) CK(launch_acm_export<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, out.p, ctx->st));
         else CK(launch_acm_export<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, out.p, ctx->st));
         ++ctx->launches;
     } else {
-        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
         CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
         const double vel = ctx->dx / ctx->lbm_dt, ps = ctx->rho * vel * vel;
         CK(launch_lbm_fields(ctx->n, ctx->perm.p, ctx->mac.p, vel, ps, ctx->scal.p + 3, out.p, ctx->st));
@@ -794,8 +926,9 @@ int rbf_set_fields(rbf_ctx *ctx, const double *uvwp) {
     DevArr<double> &in = ctx->stage;
     CK(cudaMemcpyAsync(in.p, uvwp, 4 * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
     const int slot = (ctx->parity + 1) & 1;  // read by the next pressure sweep
-    if (ctx->prec == RBF_FP32) {
-        CK(launch_acm_import<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, in.p, ctx->st));
+    if (is_f32(ctx)) {
+        if (ctx->prec == RBF_FP32C) CK(launch_acm_import_pair(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, ctx->l32[0].p, ctx->l32[1].p, ctx->l32[2].p, ctx->l32[3].p, in.p, ctx->st));
+        else CK(launch_acm_import<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, in.p, ctx->st));
         CK(acm_launch_vmax<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), slot, ctx->st));
     } else {
         CK(launch_acm_import<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, in.p, ctx->st));
@@ -811,8 +944,8 @@ int rbf_lbm_get_populations(rbf_ctx *ctx, double *f) {
     if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_get_populations: no LBM state");
     DeviceGuard dg(ctx->device);
     DevArr<double> &out = ctx->stage;
-    if (ctx->prec == RBF_FP32) CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
-    else CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
+    if (is_f32(ctx)) CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
+    else CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
     ++ctx->launches;
     CK(cudaMemcpyAsync(f, out.p, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -825,8 +958,8 @@ int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f) {
     DeviceGuard dg(ctx->device);
     DevArr<double> &in = ctx->stage;
     CK(cudaMemcpyAsync(in.p, f, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-    if (ctx->prec == RBF_FP32) CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
-    else CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    if (is_f32(ctx)) CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    else CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
     ++ctx->launches;
     CK(cudaStreamSynchronize(ctx->st));
     return RBF_OK;
@@ -877,12 +1010,12 @@ int probe_q(rbf_ctx *ctx, int m_p, double *qout) {
     int rc = ensure_probes(ctx, m_p);
     if (rc) return rc;
     if (ctx->solver == RBF_SOLVER_ACM) {
-        if (ctx->prec == RBF_FP32) CK(launch_probe_sum<float>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        if (is_f32(ctx)) CK(launch_probe_sum<float>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         else CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 2;
     } else {
-        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
         CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 3;
     }
@@ -917,7 +1050,7 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
     DeviceGuard dg(ctx->device);
     const double mu = ctx->rho * ctx->prm.nu;
     if (ctx->solver == RBF_SOLVER_ACM) {
-        if (ctx->prec == RBF_FP32) {
+        if (is_f32(ctx)) {
             FieldView<float> f{ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, 1, 1.0, 0.0, 1.0};
             CK(launch_drag<float>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
         } else {
@@ -926,8 +1059,8 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
         }
         ctx->launches += 2;
     } else {
-        if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
         CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
         double sums[4];
         CK(cudaMemcpyAsync(sums, ctx->scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -978,14 +1111,23 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
         d.idx = x->idx_sell.p; d.w = ws->p; d.type = x->type.p; d.wall = x->wall.p; d.idxb = x->idxb_sell.p; d.wn = wn->p;
         d.u = a[0].p; d.v = a[1].p; d.w_ = a[2].p; d.p = a[3].p; d.us = a[4].p; d.vs = a[5].p; d.ws = a[6].p;
         d.uo = a[7].p; d.vo = a[8].p; d.wo = a[9].p; d.vmax = x->vmax.p;
+        if constexpr (sizeof(T) == 4) {
+            if (x->prec == RBF_FP32C) {
+                DevArr<float> *l = x->l32;
+                d.ul = l[0].p; d.vl = l[1].p; d.wl = l[2].p; d.pl = l[3].p; d.usl = l[4].p; d.vsl = l[5].p;
+                d.wsl = l[6].p; d.uol = l[7].p; d.vol = l[8].p; d.wol = l[9].p;
+            }
+        }
         d.dt = (T)x->dt; d.nu = (T)x->prm.nu; d.gx = (T)x->prm.g[0]; d.gy = (T)x->prm.g[1]; d.gz = (T)x->prm.g[2];
         d.rho = (T)x->rho; d.beta = x->beta; d.vref = x->vref;
         for (int64_t s = 0; s < x->npad / 32; ++s) sl.push_back(make_int2(c, (int)s));
         for (int64_t s = 0; s < (x->nb + 31) / 32; ++s) wsl.push_back(make_int2(c, (int)s));
     }
+    const bool cp = cs[0]->prec == RBF_FP32C;
+    const int block = cs[0]->persist_block, wpb = block / 32;
     int maxb = 0;
-    CK(acm_persistent_max_blocks<T>(&maxb));
-    const int nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + 7) / 8)));
+    CK(acm_persistent_max_blocks<T>(&maxb, block, cp));
+    const int nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + wpb - 1) / wpb)));
     DevArr<CellDesc<T>> d_desc;
     DevArr<int2> d_sl, d_wsl;
     DevArr<unsigned> d_bar;
@@ -1005,9 +1147,16 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
     ctl.resid = d_res.p; ctl.partial = d_part.p; ctl.ncells = nc; ctl.nslices = (int64_t)sl.size();
     ctl.nwslices = (int64_t)wsl.size(); ctl.slices = d_sl.p; ctl.wslices = d_wsl.p; ctl.max_steps = o->max_steps;
     ctl.check_every = o->check_every > 0 ? o->check_every : 100; ctl.tol = o->tol; ctl.n_p = cs[0]->n_p;
-    CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, st));
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, cp, st));
+    CK(cudaEventRecord(ctx->ev1, st));
     for (rbf_ctx *x : cs) x->launches += 1;
     CK(cudaStreamSynchronize(st));
+    {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        ctx->persist_ms = ms;
+    }
     int32_t e = 0;
     steps.assign(nc, 0); resid.assign(nc, 0.0); done.assign(nc, 0);
     CK(cudaMemcpy(&e, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1032,7 +1181,7 @@ int persistent_solve(std::vector<rbf_ctx *> &cs, const rbf_solve_opts *o, std::v
             x->device != cs[0]->device)
             return RBF_EINVAL;
     if ((int)cs.size() > PERSIST_MAX_CELLS) return RBF_EINVAL;
-    if (cs[0]->prec == RBF_FP32) return persistent_solve_T<float>(cs, cs[0]->st, o, steps, resid, done, err);
+    if (is_f32(cs[0])) return persistent_solve_T<float>(cs, cs[0]->st, o, steps, resid, done, err);
     return persistent_solve_T<double>(cs, cs[0]->st, o, steps, resid, done, err);
 }
 
@@ -1070,48 +1219,25 @@ int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
         res->k_over_d2 = k;
         return res->converged ? RBF_OK : fail(ctx, RBF_ENOTCONVERGED, "rbf_solve: step cap reached");
     }
+    // MLBM: stop when k/d^2 changes by less than tol between checks
     while (done < opts->max_steps) {
-        int64_t chunk = std::min<int64_t>(every, opts->max_steps - done);
-        double crit = NAN;
-        if (ctx->solver == RBF_SOLVER_ACM) {
-            int rc = run_steps(ctx, chunk - 1);
-            if (rc) return rc;
-            if (ctx->prec == RBF_FP32) for (int a = 0; a < 3; ++a) CK(cudaMemcpyAsync(ctx->a32[7 + a].p, ctx->a32[a].p, ctx->npad * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
-            else for (int a = 0; a < 3; ++a) CK(cudaMemcpyAsync(ctx->a64[7 + a].p, ctx->a64[a].p, ctx->npad * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-            rc = run_steps(ctx, 1);
-            if (rc) return rc;
-            if (ctx->prec == RBF_FP32) CK(launch_residual<float>(ctx->n, ctx->type.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[7].p, ctx->a32[8].p, ctx->a32[9].p, ctx->partial.p, ctx->scal.p + 12, ctx->st));
-            else CK(launch_residual<double>(ctx->n, ctx->type.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[7].p, ctx->a64[8].p, ctx->a64[9].p, ctx->partial.p, ctx->scal.p + 12, ctx->st));
-            ctx->launches += 2;
-            double r2[2];
-            CK(cudaMemcpyAsync(r2, ctx->scal.p + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-            CK(cudaStreamSynchronize(ctx->st));
-            done += chunk;
-            if (!std::isfinite(r2[0]) || !std::isfinite(r2[1])) {
-                res->steps = done;
-                return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite velocity");
-            }
-            crit = r2[1] > 0.0 ? std::sqrt(r2[0]) / std::sqrt(r2[1]) : 0.0;
-            res->residual = crit;
-            if (crit < opts->tol && r2[1] > 0.0) { res->converged = 1; break; }
-        } else {
-            int rc = run_steps(ctx, chunk);
-            if (rc) return rc;
-            done += chunk;
-            double k = 0.0;
-            rc = rbf_permeability(ctx, m_p, &k, nullptr);
-            if (rc) return rc;
-            if (!std::isfinite(k)) {
-                res->steps = done;
-                return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite permeability");
-            }
-            if (std::isfinite(kprev) && k != 0.0) {
-                crit = std::fabs(k - kprev) / std::fabs(k);
-                res->residual = crit;
-                if (crit < opts->tol) { kprev = k; res->converged = 1; break; }
-            }
-            kprev = k;
+        const int64_t chunk = std::min<int64_t>(every, opts->max_steps - done);
+        int rc = run_steps(ctx, chunk);
+        if (rc) return rc;
+        done += chunk;
+        double k = 0.0;
+        rc = rbf_permeability(ctx, m_p, &k, nullptr);
+        if (rc) return rc;
+        if (!std::isfinite(k)) {
+            res->steps = done;
+            return fail(ctx, RBF_EDIVERGED, "rbf_solve: non-finite permeability");
         }
+        if (std::isfinite(kprev) && k != 0.0) {
+            const double crit = std::fabs(k - kprev) / std::fabs(k);
+            res->residual = crit;
+            if (crit < opts->tol) { kprev = k; res->converged = 1; break; }
+        }
+        kprev = k;
     }
     res->steps = done;
     double k = 0.0;
@@ -1197,13 +1323,13 @@ extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2,
     double s = 0.0;
     if (nb > 0) {
         if (ctx->solver == RBF_SOLVER_ACM) {
-            if (ctx->prec == RBF_FP32)
+            if (is_f32(ctx))
                 k_probe_sum_static<float><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, scratch);
             else
                 k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, scratch);
         } else {
-            if (ctx->prec == RBF_FP32) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-            else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+            if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+            else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
             ++ctx->launches;
             k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, scratch);
         }
@@ -1374,6 +1500,16 @@ int rbf_batch_init(rbf_batch *b, const rbf_params *p) {
         if (rc) return bfail(b, rc, b->cells[c]->err);
     }
     return RBF_OK;
+}
+
+int rbf_batch_autotune(rbf_batch *b, int trial_steps, rbf_tune_report *rep) {
+    if (!b) return RBF_EINVAL;
+    if (b->cells.empty() || !b->cells[0]->inited) return bfail(b, RBF_EINVAL, "rbf_batch_autotune: init first");
+    if (trial_steps < 2 || trial_steps > 20000) return bfail(b, RBF_EINVAL, "rbf_batch_autotune: 2 <= trial_steps <= 20000");
+    DeviceGuard dg(b->device);
+    std::string msg;
+    const int rc = tune_persistent(b->cells, trial_steps, rep, msg);
+    return rc ? bfail(b, rc, msg.empty() ? std::string("rbf_batch_autotune failed") : msg) : RBF_OK;
 }
 
 int rbf_batch_solve(rbf_batch *b, const rbf_solve_opts *opts, rbf_batch_cell_result *res) {

@@ -69,6 +69,7 @@ struct rbf_ctx {
     double dt = 0.0, vref = 0.0, beta = 10.0, rho = 1.0;
     int n_p = 3, parity = 0;
     DevArr<float> a32[10];
+    DevArr<float> l32[10];   // RBF_FP32C: low words of a32 (allocated only in that mode)
     DevArr<double> a64[10];
     DevArr<unsigned long long> vmax;
     double tp = 0.8, tm = 1.125, gl[3] = {0, 0, 0}, lbm_dt = 0.0;
@@ -87,7 +88,10 @@ struct rbf_ctx {
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1;
     int variant = rbf::LBM_PAIR_PER_WARP;  // schedule of the fused LBM step
+    int lbm_layout = rbf::LBM_LAYOUT_PAIRS;  // layout of f32 / f64 (follows the schedule)
     int acm_block = 256;              // threads per block of the ACM sweeps
+    int persist_block = 256;          // threads per block of the persistent ACM driver
+    double persist_ms = 0.0;          // device time of its last launch
     int gblock = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;

@@ -8,7 +8,7 @@
 #define RBF_MAX_NL 64         // largest stencil
 #define RBF_MAX_NP 35         // monomials for m <= 4
 #define RBF_MAX_NS (RBF_MAX_NL + RBF_MAX_NP)
-#define RBF_MAX_OPS 32        // right-hand sides per saddle system (one lane each)
+#define RBF_MAX_OPS 32        // right-hand sides per saddle system
 
 namespace rbf {
 

@@ -56,9 +56,13 @@ double host_lattice_weight(int q, int k) { return q == 15 ? VSet<15>::w(k) : VSe
 // opposite of k: k+1 for odd k, k-1 for even k >= 2, 0 for 0
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
 
-// Population k of node i: the rest population in [0, npad), then the opposite
-// pairs (k, k') = (2p+1, 2p+2) interleaved, pair p at npad + 2 (p npad + i) + {0, 1}.
-__host__ __device__ __forceinline__ int64_t pop_at(int k, int64_t i, int64_t npad) {
+// Population k of node i.  Pairs layout: the rest population in [0, npad),
+// then the opposite pairs (k, k') = (2p+1, 2p+2) interleaved, pair p at
+// npad + 2 (p npad + i) + {0, 1}.  Node layout: the q populations of node i in
+// one record of lbm_rec_len(q) values at i lbm_rec_len(q) (padding zero), so a
+// neighbour's populations arrive in a few 16-byte loads.
+__host__ __device__ __forceinline__ int64_t pop_at(int k, int64_t i, int64_t npad, int layout, int q) {
+    if (layout == LBM_LAYOUT_NODES) return i * lbm_rec_len(q) + k;
     return k == 0 ? i : npad + 2 * ((int64_t)((k - 1) >> 1) * npad + i) + ((k - 1) & 1);
 }
 
@@ -164,6 +168,75 @@ __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
         o.y = f[2 * p + 2];
         op2[p * np + i] = o;
     }
+}
+
+template <typename T> struct Vec16;  // 16-byte vector of T
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    static __device__ __forceinline__ void get(const float4 &v, float *d) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+    static __device__ __forceinline__ float4 make(const float *d) { return make_float4(d[0], d[1], d[2], d[3]); }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    static __device__ __forceinline__ void get(const double2 &v, double *d) { d[0] = v.x; d[1] = v.y; }
+    static __device__ __forceinline__ double2 make(const double *d) { return make_double2(d[0], d[1]); }
+};
+
+// One thread per node on the node layout: each stencil column costs one index
+// load, (q-1)/2 coalesced 8-byte weight loads and lbm_rec_len(q) / 4 16-byte
+// loads of the neighbour's record (FP32 D3Q19: 5, against 9 pair gathers on the
+// pairs layout), U columns in flight.  Same arithmetic, in the same order, as
+// k_lbm_step.
+template <typename T, int Q, int U>
+__global__ void __launch_bounds__(256) k_lbm_step_records(LbmArgs<T> a) {
+    using V = typename Vec2<T>::type;
+    using W = Vec16<T>;
+    using V16 = typename W::type;
+    constexpr int NP = (Q - 1) / 2;
+    constexpr int RL = lbm_rec_len(Q);
+    constexpr int NV = RL / W::n;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int n_l = a.n_l;
+    const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
+    const V *__restrict__ wp = reinterpret_cast<const V *>(a.w) + ((s * NP * (int64_t)n_l) << 5) + lane;
+    const V16 *__restrict__ rec = reinterpret_cast<const V16 *>(a.fin);
+    T f[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) f[k] = (T)0;
+#pragma unroll U
+    for (int j = 0; j < n_l; ++j) {
+        const int q = __ldg(ip + (j << 5));
+        T g[RL];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) W::get(__ldg(rec + (int64_t)q * NV + v), g + v * W::n);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const V w2 = __ldcs(wp + ((p * n_l + j) << 5));
+            f[2 * p + 1] += w2.x * g[2 * p + 1];
+            f[2 * p + 2] += w2.y * g[2 * p + 2];
+        }
+    }
+    f[0] = a.fin[i * RL];
+    const uint32_t m = a.mask[i];
+    if (m) {
+#pragma unroll
+        for (int k = 1; k < Q; ++k)
+            if (m & (1u << k)) f[k] = f[opp(k)];
+    }
+    trt_collide<T, Q>(f, a.tp_inv, a.tm_inv, a.gx, a.gy, a.gz);
+    T o[RL];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) o[k] = f[k];
+#pragma unroll
+    for (int k = Q; k < RL; ++k) o[k] = (T)0;
+    V16 *__restrict__ out = reinterpret_cast<V16 *>(a.fout) + i * NV;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = W::make(o + v * W::n);
 }
 
 // Pair-per-warp variant.  A block owns one SELL slice (32 nodes, one per lane)
@@ -275,38 +348,52 @@ __global__ void k_lbm_init(LbmArgs<T> a) {
     for (int k = 0; k < Q; ++k) f[k] = (T)0;
     trt_collide<T, Q>(f, a.tp_inv, a.tm_inv, a.gx, a.gy, a.gz);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) a.fout[pop_at(k, i, a.npad)] = i < a.n ? f[k] : (T)0;
+    for (int k = 0; k < Q; ++k) a.fout[pop_at(k, i, a.npad, a.layout, Q)] = i < a.n ? f[k] : (T)0;
+    if (a.layout == LBM_LAYOUT_NODES)
+        for (int k = Q; k < lbm_rec_len(Q); ++k) a.fout[i * lbm_rec_len(Q) + k] = (T)0;
 }
 
 // populations <-> FP64 unshifted, caller's order (perm: sorted -> caller)
 template <typename T, int Q>
-__global__ void k_lbm_export(int64_t n, int64_t npad, const T *__restrict__ f, const int32_t *__restrict__ perm, double *out) {
+__global__ void k_lbm_export(int64_t n, int64_t npad, int layout, const T *__restrict__ f,
+                             const int32_t *__restrict__ perm, double *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t o = perm[i];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) out[k * n + o] = (double)f[pop_at(k, i, npad)] + VSet<Q>::w(k);
+    for (int k = 0; k < Q; ++k) out[k * n + o] = (double)f[pop_at(k, i, npad, layout, Q)] + VSet<Q>::w(k);
 }
 template <typename T, int Q>
-__global__ void k_lbm_import(int64_t n, int64_t npad, T *f, const int32_t *__restrict__ perm, const double *in) {
+__global__ void k_lbm_import(int64_t n, int64_t npad, int layout, T *f, const int32_t *__restrict__ perm,
+                             const double *in) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t o = perm[i];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) f[pop_at(k, i, npad)] = (T)(in[k * n + o] - VSet<Q>::w(k));
+    for (int k = 0; k < Q; ++k) f[pop_at(k, i, npad, layout, Q)] = (T)(in[k * n + o] - VSet<Q>::w(k));
+}
+template <typename T, int Q>
+__global__ void k_lbm_relayout(int64_t npad, int from, const T *__restrict__ src, int to, T *dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dst[pop_at(k, i, npad, to, Q)] = src[pop_at(k, i, npad, from, Q)];
+    if (to == LBM_LAYOUT_NODES)
+        for (int k = Q; k < lbm_rec_len(Q); ++k) dst[i * lbm_rec_len(Q) + k] = (T)0;
 }
 
 // macroscopic fields from the post-collision state: rho is unchanged by the
 // collision, the momentum gained rho g_lb, so v_lb = sum f e / rho - g_lb.
 // out (sorted order) = (vx, vy, vz, rho - 1) in lattice units, FP64.
 template <typename T, int Q>
-__global__ void k_lbm_macro(int64_t n, int64_t npad, const T *__restrict__ f, double gx, double gy, double gz, double *out) {
+__global__ void k_lbm_macro(int64_t n, int64_t npad, int layout, const T *__restrict__ f, double gx, double gy, double gz,
+                            double *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double d = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        double fk = (double)f[pop_at(k, i, npad)];
+        double fk = (double)f[pop_at(k, i, npad, layout, Q)];
         d += fk;
         mx += VSet<Q>::e(k, 0) * fk; my += VSet<Q>::e(k, 1) * fk; mz += VSet<Q>::e(k, 2) * fk;
     }
@@ -358,6 +445,10 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
     case LBM_PAIR_PER_WARP_U3: k_lbm_step_pairs<T, Q, 3><<<slices, 32 * NP, 0, st>>>(a); break;
     case LBM_PAIR_PER_WARP_U6: k_lbm_step_pairs<T, Q, 6><<<slices, 32 * NP, 0, st>>>(a); break;
     case LBM_PAIR_PER_WARP_U2: k_lbm_step_pairs<T, Q, 2><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_RECORD_PER_THREAD: k_lbm_step_records<T, Q, 1><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a); break;
+    case LBM_RECORD_PER_THREAD_128_U2:
+        k_lbm_step_records<T, Q, 2><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -365,6 +456,7 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
 
 template <typename T>
 cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int code) {
+    if (code < 0 || code >= LBM_N_SCHEDULES || lbm_layout_of(code) != a.layout) return cudaErrorInvalidValue;
     if (q == 19) return launch_step_q<T, 19>(a, st, code);
     if (q == 15) return launch_step_q<T, 15>(a, st, code);
     return cudaErrorInvalidValue;
@@ -388,35 +480,48 @@ cudaError_t lbm_launch_masks(int64_t n, int q, const uint8_t *type, const double
 }
 
 template <typename T>
-cudaError_t lbm_launch_export(int64_t n, int64_t npad, int q, const T *f, const int32_t *perm, double *out, cudaStream_t st) {
+cudaError_t lbm_launch_export(int64_t n, int64_t npad, int layout, int q, const T *f, const int32_t *perm, double *out,
+                              cudaStream_t st) {
     unsigned g = (unsigned)((n + 255) / 256);
-    if (q == 19) k_lbm_export<T, 19><<<g, 256, 0, st>>>(n, npad, f, perm, out);
-    else k_lbm_export<T, 15><<<g, 256, 0, st>>>(n, npad, f, perm, out);
+    if (q == 19) k_lbm_export<T, 19><<<g, 256, 0, st>>>(n, npad, layout, f, perm, out);
+    else k_lbm_export<T, 15><<<g, 256, 0, st>>>(n, npad, layout, f, perm, out);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t lbm_launch_import(int64_t n, int64_t npad, int q, T *f, const int32_t *perm, const double *in, cudaStream_t st) {
+cudaError_t lbm_launch_import(int64_t n, int64_t npad, int layout, int q, T *f, const int32_t *perm, const double *in,
+                              cudaStream_t st) {
     unsigned g = (unsigned)((n + 255) / 256);
-    if (q == 19) k_lbm_import<T, 19><<<g, 256, 0, st>>>(n, npad, f, perm, in);
-    else k_lbm_import<T, 15><<<g, 256, 0, st>>>(n, npad, f, perm, in);
+    if (q == 19) k_lbm_import<T, 19><<<g, 256, 0, st>>>(n, npad, layout, f, perm, in);
+    else k_lbm_import<T, 15><<<g, 256, 0, st>>>(n, npad, layout, f, perm, in);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t lbm_launch_macro(int64_t n, int64_t npad, int q, const T *f, const double g[3], double *out, cudaStream_t st) {
+cudaError_t lbm_launch_relayout(int64_t npad, int q, int from, const T *src, int to, T *dst, cudaStream_t st) {
+    unsigned g = (unsigned)((npad + 255) / 256);
+    if (q == 19) k_lbm_relayout<T, 19><<<g, 256, 0, st>>>(npad, from, src, to, dst);
+    else if (q == 15) k_lbm_relayout<T, 15><<<g, 256, 0, st>>>(npad, from, src, to, dst);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t lbm_launch_macro(int64_t n, int64_t npad, int layout, int q, const T *f, const double g[3], double *out,
+                             cudaStream_t st) {
     unsigned gr = (unsigned)((n + 255) / 256);
-    if (q == 19) k_lbm_macro<T, 19><<<gr, 256, 0, st>>>(n, npad, f, g[0], g[1], g[2], out);
-    else k_lbm_macro<T, 15><<<gr, 256, 0, st>>>(n, npad, f, g[0], g[1], g[2], out);
+    if (q == 19) k_lbm_macro<T, 19><<<gr, 256, 0, st>>>(n, npad, layout, f, g[0], g[1], g[2], out);
+    else k_lbm_macro<T, 15><<<gr, 256, 0, st>>>(n, npad, layout, f, g[0], g[1], g[2], out);
     return cudaGetLastError();
 }
 
 #define RBF_LBM_INST(T)                                                                                         \
     template cudaError_t lbm_launch_step<T>(const LbmArgs<T> &, int, cudaStream_t, int);                        \
     template cudaError_t lbm_launch_init<T>(const LbmArgs<T> &, int, cudaStream_t);                             \
-    template cudaError_t lbm_launch_export<T>(int64_t, int64_t, int, const T *, const int32_t *, double *,      \
+    template cudaError_t lbm_launch_export<T>(int64_t, int64_t, int, int, const T *, const int32_t *, double *, \
                                               cudaStream_t);                                                    \
-    template cudaError_t lbm_launch_import<T>(int64_t, int64_t, int, T *, const int32_t *, const double *,      \
+    template cudaError_t lbm_launch_import<T>(int64_t, int64_t, int, int, T *, const int32_t *, const double *, \
                                               cudaStream_t);                                                    \
-    template cudaError_t lbm_launch_macro<T>(int64_t, int64_t, int, const T *, const double *, double *, cudaStream_t);
+    template cudaError_t lbm_launch_relayout<T>(int64_t, int, int, const T *, int, T *, cudaStream_t);          \
+    template cudaError_t lbm_launch_macro<T>(int64_t, int64_t, int, int, const T *, const double *, double *,   \
+                                             cudaStream_t);
 RBF_LBM_INST(float)
 RBF_LBM_INST(double)
 

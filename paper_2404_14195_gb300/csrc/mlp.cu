@@ -343,15 +343,15 @@ __global__ void k_incr(int64_t *a, int64_t *b) {
 // warm start: predicted (u, v, w, p) into ACM fields of type T (sorted node order),
 // zero velocity on wall nodes
 template <typename T>
-__global__ void k_inject(int64_t n, const float *__restrict__ pred, const uint8_t *__restrict__ type, float scale,
+__global__ void k_inject(int64_t n, const float *__restrict__ pred, const uint8_t *__restrict__ type, float4 scale,
                          T *u, T *v, T *w, T *p) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool wall = type[i] != 0;
-    u[i] = wall ? (T)0 : (T)(scale * pred[4 * i]);
-    v[i] = wall ? (T)0 : (T)(scale * pred[4 * i + 1]);
-    w[i] = wall ? (T)0 : (T)(scale * pred[4 * i + 2]);
-    p[i] = (T)(scale * pred[4 * i + 3]);
+    u[i] = wall ? (T)0 : (T)(scale.x * pred[4 * i]);
+    v[i] = wall ? (T)0 : (T)(scale.y * pred[4 * i + 1]);
+    w[i] = wall ? (T)0 : (T)(scale.z * pred[4 * i + 2]);
+    p[i] = (T)(scale.w * pred[4 * i + 3]);
 }
 // radius and signed wall distance of the context's nodes (sorted order)
 __global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx, double cy, double cz, double r,
@@ -748,8 +748,8 @@ int rbf_mlp_predict(rbf_mlp *mm, int64_t n, const double *xyz, const float *radi
     return check_err(mm);
 }
 
-int rbf_mlp_warm_start(rbf_mlp *mm, rbf_ctx *ctx, double scale) {
-    if (!mm || !ctx) return RBF_EINVAL;
+int rbf_mlp_warm_start(rbf_mlp *mm, rbf_ctx *ctx, const double *scale) {
+    if (!mm || !ctx || !scale) return RBF_EINVAL;
     if (!ctx->inited || ctx->solver != RBF_SOLVER_ACM) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: needs an initialised ACM context");
     if (!ctx->has_sphere) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: the context has no sphere");
     if (ctx->device != mm->device) return mfail(mm, RBF_EINVAL, "rbf_mlp_warm_start: different devices");
@@ -777,16 +777,19 @@ int rbf_mlp_warm_start(rbf_mlp *mm, rbf_ctx *ctx, double scale) {
         MCK(cudaStreamSynchronize(mm->st));
     }
     const unsigned gb = (unsigned)((n + 255) / 256);
-    if (ctx->prec == RBF_FP32)
-        k_inject<float><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, (float)scale, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p);
+    const float4 sc = make_float4((float)scale[0], (float)scale[1], (float)scale[2], (float)scale[3]);
+    if (ctx->prec != RBF_FP64)
+        k_inject<float><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, sc, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p);
     else
-        k_inject<double><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, (float)scale, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p);
+        k_inject<double><<<gb, 256, 0, mm->st>>>(n, predall.p, ctx->type.p, sc, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p);
     ++mm->launches;
+    if (ctx->prec == RBF_FP32C)
+        for (int c = 0; c < 4; ++c) MCK(ctx->l32[c].zero(mm->st));
     MCK(cudaGetLastError());
     MCK(cudaStreamSynchronize(mm->st));
     // C of Eq. MNS_C from the new velocity, in the slot the next pressure sweep reads
     const int slot = (ctx->parity + 1) & 1;
-    if (ctx->prec == RBF_FP32) {
+    if (ctx->prec != RBF_FP64) {
         AcmArgs<float> a;
         std::memset(&a, 0, sizeof(a));
         a.n = n; a.u = ctx->a32[0].p; a.v = ctx->a32[1].p; a.w_ = ctx->a32[2].p; a.vmax = ctx->vmax.p;

@@ -207,6 +207,44 @@ cudaError_t launch_acm_import(int64_t n, const int32_t *perm, T *u, T *v, T *w, 
     return cudaGetLastError();
 }
 
+__global__ void k_acm_export_pair(int64_t n, const int32_t *perm, const float *u, const float *v, const float *w,
+                                  const float *p, const float *ul, const float *vl, const float *wl, const float *pl,
+                                  double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = perm[i];
+    out[4 * o] = (double)u[i] + (double)ul[i];
+    out[4 * o + 1] = (double)v[i] + (double)vl[i];
+    out[4 * o + 2] = (double)w[i] + (double)wl[i];
+    out[4 * o + 3] = (double)p[i] + (double)pl[i];
+}
+__device__ __forceinline__ void split_pair(double x, float *hi, float *lo, int64_t i) {
+    const float h = (float)x;
+    hi[i] = h;
+    lo[i] = (float)(x - (double)h);
+}
+__global__ void k_acm_import_pair(int64_t n, const int32_t *perm, float *u, float *v, float *w, float *p, float *ul,
+                                  float *vl, float *wl, float *pl, const double *in) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = perm[i];
+    split_pair(in[4 * o], u, ul, i);
+    split_pair(in[4 * o + 1], v, vl, i);
+    split_pair(in[4 * o + 2], w, wl, i);
+    split_pair(in[4 * o + 3], p, pl, i);
+}
+cudaError_t launch_acm_export_pair(int64_t n, const int32_t *perm, const float *u, const float *v, const float *w,
+                                   const float *p, const float *ul, const float *vl, const float *wl,
+                                   const float *pl, double *out, cudaStream_t st) {
+    k_acm_export_pair<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, u, v, w, p, ul, vl, wl, pl, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_acm_import_pair(int64_t n, const int32_t *perm, float *u, float *v, float *w, float *p,
+                                   float *ul, float *vl, float *wl, float *pl, const double *in, cudaStream_t st) {
+    k_acm_import_pair<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, u, v, w, p, ul, vl, wl, pl, in);
+    return cudaGetLastError();
+}
+
 // LBM macro buffer (sorted, lattice units, (vx, vy, vz, drho)) -> physical uvwp, caller order
 __global__ void k_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
                              const double *drho_sum, double *out) {

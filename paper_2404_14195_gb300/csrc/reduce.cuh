@@ -30,6 +30,13 @@ cudaError_t launch_acm_export(int64_t n, const int32_t *perm, const T *u, const 
 template <typename T>
 cudaError_t launch_acm_import(int64_t n, const int32_t *perm, T *u, T *v, T *w, T *p, const double *in,
                               cudaStream_t st);
+// compensated FP32 fields: exports hi + lo in FP64; imports x as hi = fl(x),
+// lo = fl(x - hi)
+cudaError_t launch_acm_export_pair(int64_t n, const int32_t *perm, const float *u, const float *v, const float *w,
+                                   const float *p, const float *ul, const float *vl, const float *wl,
+                                   const float *pl, double *out, cudaStream_t st);
+cudaError_t launch_acm_import_pair(int64_t n, const int32_t *perm, float *u, float *v, float *w, float *p,
+                                   float *ul, float *vl, float *wl, float *pl, const double *in, cudaStream_t st);
 template <typename T>
 cudaError_t launch_nonfinite(const T *a, int64_t n, int32_t *flag, cudaStream_t st);
 cudaError_t launch_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,

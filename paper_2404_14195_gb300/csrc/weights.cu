@@ -6,8 +6,8 @@
 //   P_jl = p_l(xi_j)            (monomials of degree <= m, graded lexicographic)
 //   M = [[A, P], [P^T, 0]]
 // factors it by LU with partial pivoting (warp-parallel rank-1 updates), and
-// solves one right-hand side per lane for up to 32 operators L (Eq.
-// operatorApprox):
+// solves the right-hand sides of up to RBF_MAX_OPS operators L (Eq.
+// operatorApprox) together, the warp's lanes spread over (row, operator) pairs:
 //   b_j = (L Phi_j)(y), c_l = (L p_l)(y),  y = x_c + off
 // followed by one step of iterative refinement whose residual is accumulated
 // with the compensated dot product Dot2 (Ogita, Rump & Oishi, SIAM J. Sci.
@@ -64,22 +64,37 @@ __device__ double mono_rhs(int kind, int a, int b, int c, double ex, double ey, 
     }
 }
 
-// Solve with the in-place LU (rows swapped as recorded in piv), one column of a
-// row-major [ns][stride] right-hand-side block.
-__device__ void lu_solve_col(int ns, int ld, const double *M, const int *piv, double *x, int stride) {
-    for (int c = 0; c < ns; ++c) {
-        int p = piv[c];
-        if (p != c) { double t = x[c * stride]; x[c * stride] = x[p * stride]; x[p * stride] = t; }
+// Solve with the in-place LU (rows swapped as recorded in piv) for all n_rhs
+// columns of the row-major [ns][n_rhs] block X at once, by the whole warp:
+// forward elimination with the unit lower factor, then back substitution with
+// the upper one, both column by column so that every step is one warp-wide
+// update over the (row, column) pairs below (above) the pivot.  Each entry sees
+// its subtractions in the order of a row-oriented substitution in the forward
+// pass and in decreasing column order in the backward pass.
+__device__ void lu_solve_warp(int ns, int ld, const double *M, const int *piv, double *X, int n_rhs, int lane) {
+    for (int o = lane; o < n_rhs; o += 32)
+        for (int c = 0; c < ns; ++c) {
+            const int p = piv[c];
+            if (p != c) { double t = X[c * n_rhs + o]; X[c * n_rhs + o] = X[p * n_rhs + o]; X[p * n_rhs + o] = t; }
+        }
+    __syncwarp();
+    for (int c = 0; c < ns - 1; ++c) {
+        const int cnt = (ns - c - 1) * n_rhs;
+        for (int e = lane; e < cnt; e += 32) {
+            const int r = c + 1 + e / n_rhs, o = e - (r - c - 1) * n_rhs;
+            X[r * n_rhs + o] -= M[r * ld + c] * X[c * n_rhs + o];
+        }
+        __syncwarp();
     }
-    for (int r = 1; r < ns; ++r) {
-        double v = x[r * stride];
-        for (int t = 0; t < r; ++t) v -= M[r * ld + t] * x[t * stride];
-        x[r * stride] = v;
-    }
-    for (int r = ns - 1; r >= 0; --r) {
-        double v = x[r * stride];
-        for (int t = r + 1; t < ns; ++t) v -= M[r * ld + t] * x[t * stride];
-        x[r * stride] = v / M[r * ld + r];
+    for (int c = ns - 1; c >= 0; --c) {
+        for (int o = lane; o < n_rhs; o += 32) X[c * n_rhs + o] /= M[c * ld + c];
+        __syncwarp();
+        const int cnt = c * n_rhs;
+        for (int e = lane; e < cnt; e += 32) {
+            const int r = e / n_rhs, o = e - r * n_rhs;
+            X[r * n_rhs + o] -= M[r * ld + c] * X[c * n_rhs + o];
+        }
+        __syncwarp();
     }
 }
 
@@ -191,36 +206,43 @@ __device__ void weights_one(int64_t c, double *smem_w, const double *__restrict_
         return;
     }
     __syncwarp();
-    // right-hand sides: lane o owns operator o
-    if (lane < n_ops) {
-        const int o = lane;
+    // right-hand sides R[r][o] (row r of operator o), warp-wide over (r, o)
+    for (int e = lane; e < ns * n_ops; e += 32) {
+        const int r = e / n_ops, o = e - r * n_ops;
         const OpSpec op = ops[o];
         const double ex = op.off[0] / delta, ey = op.off[1] / delta, ez = op.off[2] / delta;
-        for (int j = 0; j < n_l; ++j)
-            R[j * n_ops + o] = rbf_rhs(op.kind, k, ex - xi[3 * j], ey - xi[3 * j + 1], ez - xi[3 * j + 2], delta);
-        for (int l = 0; l < np; ++l) {
-            int a, b, cc; mono_exp(l, &a, &b, &cc);
-            R[(n_l + l) * n_ops + o] = mono_rhs(op.kind, a, b, cc, ex, ey, ez, delta);
+        double v;
+        if (r < n_l) {
+            v = rbf_rhs(op.kind, k, ex - xi[3 * r], ey - xi[3 * r + 1], ez - xi[3 * r + 2], delta);
+        } else {
+            int a, b, cc; mono_exp(r - n_l, &a, &b, &cc);
+            v = mono_rhs(op.kind, a, b, cc, ex, ey, ez, delta);
         }
-        for (int r = 0; r < ns; ++r) X[r * n_ops + o] = R[r * n_ops + o];
-        lu_solve_col(ns, ld, M, piv, X + o, n_ops);
-        for (int it = 0; it < refine; ++it) {
-            for (int r = 0; r < ns; ++r) {  // D = rhs - M0 x, compensated (Dot2)
-                double s = R[r * n_ops + o], cmp = 0.0;
-                for (int q = 0; q < ns; ++q) {
-                    double a = M0[r * ld + q], x = X[q * n_ops + o];
-                    double p = -a * x;
-                    double pe = fma(-a, x, -p);  // -a x = p + pe exactly
-                    double t = s + p;
-                    double z = t - s;
-                    cmp += ((s - (t - z)) + (p - z)) + pe;
-                    s = t;
-                }
-                D[r * n_ops + o] = s + cmp;
+        R[e] = v;
+        X[e] = v;
+    }
+    __syncwarp();
+    lu_solve_warp(ns, ld, M, piv, X, n_ops, lane);
+    for (int it = 0; it < refine; ++it) {
+        // D = rhs - M0 x, each entry a compensated dot product (Dot2), warp-wide over (r, o)
+        for (int e = lane; e < ns * n_ops; e += 32) {
+            const int r = e / n_ops, o = e - r * n_ops;
+            double s = R[e], cmp = 0.0;
+            for (int q = 0; q < ns; ++q) {
+                const double a = M0[r * ld + q], x = X[q * n_ops + o];
+                const double p = -a * x;
+                const double pe = fma(-a, x, -p);  // -a x = p + pe exactly
+                const double t = s + p;
+                const double z = t - s;
+                cmp += ((s - (t - z)) + (p - z)) + pe;
+                s = t;
             }
-            lu_solve_col(ns, ld, M, piv, D + o, n_ops);
-            for (int r = 0; r < ns; ++r) X[r * n_ops + o] += D[r * n_ops + o];
+            D[e] = s + cmp;
         }
+        __syncwarp();
+        lu_solve_warp(ns, ld, M, piv, D, n_ops, lane);
+        for (int e = lane; e < ns * n_ops; e += 32) X[e] += D[e];
+        __syncwarp();
     }
     __syncwarp();
     for (int e = lane; e < n_ops * n_l; e += 32) {

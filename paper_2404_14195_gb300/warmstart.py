@@ -8,7 +8,7 @@ import time
 
 import numpy as np
 
-from . import RBF_FP32, Batch, Mlp, Solver
+from . import RBF_FP32C, Batch, Mlp, Solver
 
 N_L_DEFAULT = 25
 
@@ -20,7 +20,7 @@ def signed_distance(xyz, centre, r):
 
 
 def steady_training_set(cases, n_l=N_L_DEFAULT, tol=1e-6, max_steps=2_000_000, check_every=1000,
-                        precision=RBF_FP32, device=0):
+                        precision=RBF_FP32C, device=0):
     """Solve every case to steady state in one batched persistent launch; returns
     (xyz, radius, sdf, targets (u, v, w, p)) over all nodes, the per-cell results
     and the wall time."""
@@ -42,16 +42,31 @@ def steady_training_set(cases, n_l=N_L_DEFAULT, tol=1e-6, max_steps=2_000_000, c
     return (np.concatenate(X), np.concatenate(R), np.concatenate(S), np.concatenate(T)), res, time.perf_counter() - t0
 
 
-def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0):
+def output_scale(targets):
+    """Per-output normalisation of the targets (u, v, w, p): their RMS over the
+    training set, so that every output weighs alike in the squared-error loss."""
+    t = np.asarray(targets, np.float64)
+    s = np.sqrt((t * t).mean(0))
+    return np.where(s > 0.0, s, 1.0)
+
+
+def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0, normalise=True):
+    """Train the network on (xyz, radius, sdf, targets); with `normalise` each
+    output is divided by its RMS for training and the network's out_scale set to
+    match, so warm_start writes fields in the solver's units."""
     m = Mlp(device)
     m.set_params(np.asarray(init_params, np.float32))
-    m.set_data(*data)
+    xyz, rad, sdf, tgt = data
+    if normalise:
+        m.out_scale = output_scale(tgt)
+        tgt = (np.asarray(tgt, np.float64) / m.out_scale).astype(np.float32)
+    m.set_data(xyz, rad, sdf, tgt)
     t0 = time.perf_counter()
     hist = m.train(steps, batch, lr, seed)
     return m, hist, time.perf_counter() - t0
 
 
-def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32, tol=1e-6, max_steps=2_000_000,
+def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32C, tol=1e-6, max_steps=2_000_000,
                check_every=1000, m_p=24, device=0):
     """Steady solve of one case from a zero start or from the network's prediction."""
     s = Solver(device)

@@ -97,3 +97,61 @@ def test_batch_converges_per_cell(rbf):
         r1 = s.solve(400000, 2e-6, check_every=200, m_p=16)
         assert r1["converged"] and r1["steps"] == res[i]["steps"]
         assert abs(r1["k_over_d2"] - res[i]["k_over_d2"]) <= 1e-5 * abs(r1["k_over_d2"])
+
+
+def test_persistent_block_sizes_give_the_same_fields(rbf):
+    case = synth.jittered_cell(r=0.35, n_axis=14, seed=5)
+    orc = oracle_acm_setup(case, 25)
+    dt = oracle.acm_dt(orc["h_min"], 1.0)
+    want, _ = oracle.acm_run(case, orc["idx"], orc["w4"], orc["idxb"], orc["wgb"], np.zeros((case.n, 4)), 120,
+                             dt=dt, v_ref=0.01)
+    s = rbf.Solver(0)
+    s.set_case(case)
+    s.build_stencils(25)
+    s.compute_weights(solver=rbf.RBF_SOLVER_ACM)
+    fields = []
+    for block in (256, 128, 64, 32):
+        s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=0.01)
+        s.set_persistent_block(block)
+        r = s.solve(120, 1e-300, check_every=40)
+        assert r["steps"] == 120
+        fields.append(s.get_fields())
+    for f in fields[1:]:
+        assert np.array_equal(f, fields[0])  # block size changes no field arithmetic
+    for c in range(4):
+        assert rel_inf(fields[0][:, c], want[:, c]) <= 1e-9, c
+    # the tuner restores the state and keeps one of the candidates
+    before = s.get_fields()
+    times, chosen = s.autotune_persistent(50)
+    assert set(times) == {256, 128, 64, 32} and chosen in times
+    assert np.array_equal(s.get_fields(), before)
+    s.step(10)
+    want2, _ = oracle.acm_run(case, orc["idx"], orc["w4"], orc["idxb"], orc["wgb"], want, 10, dt=dt, v_ref=0.01)
+    got2 = s.get_fields()
+    for c in range(4):
+        assert rel_inf(got2[:, c], want2[:, c]) <= 1e-9, c
+
+
+def test_batch_more_cells_than_threads_per_block(rbf):
+    """40 small cells with 32-thread blocks: block 0's per-cell bookkeeping loops
+    over more cells than it has threads."""
+    rng = np.random.default_rng(12)
+    cells = [(synth.jittered_cell(r=float(r), n_axis=7, seed=700 + i), 20) for i, r in enumerate(rng.uniform(0.2, 0.4, 40))]
+    b = rbf.Batch(0)
+    for case, n_l in cells:
+        b.add_cell(case, n_l)
+    assert b.build(3, 2)["n_singular"] == 0
+    b.init(precision=rbf.RBF_FP64, v_ref=0.01)
+    b.set_persistent_block(32)
+    res = b.solve(60, 1e-300, check_every=20)
+    assert [r["steps"] for r in res] == [60] * 40
+    for i in (0, 17, 33, 39):
+        case, n_l = cells[i]
+        orc = oracle_acm_setup(case, n_l)
+        dt = oracle.acm_dt(orc["h_min"], 1.0)
+        want, r_o = oracle.acm_run(case, orc["idx"], orc["w4"], orc["idxb"], orc["wgb"], np.zeros((case.n, 4)), 60,
+                                   dt=dt, v_ref=0.01)
+        got = b.cell(i).get_fields()
+        for c in range(4):
+            assert rel_inf(got[:, c], want[:, c]) <= 1e-9, (i, c)
+        assert abs(res[i]["residual"] - r_o[-1]) <= 1e-6 * r_o[-1], i

@@ -136,7 +136,8 @@ def _lbm_case(rbf, cell, q, prec, g_phys, n_l=25):
     return s, u, idx, wk, dx
 
 
-@pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0), (19, 2), (19, 3), (19, 4), (15, 5)])
+@pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0), (19, 2), (19, 3), (19, 4), (15, 5),
+                                       (19, 6), (15, 6), (19, 7), (15, 7)])
 def test_lbm_fp64_populations(rbf, cell, q, variant):
     # g large enough that f - omega is far above rounding (parity of the arithmetic)
     g = (2e4, 5e3, 0.0)
@@ -159,7 +160,7 @@ def test_lbm_fp64_populations(rbf, cell, q, variant):
     assert rel_inf(fields[:, 3], p_want) <= 1e-8
 
 
-@pytest.mark.parametrize("variant", [1, 0])
+@pytest.mark.parametrize("variant", [1, 0, 6, 7])
 def test_lbm_fp32_populations(rbf, cell, variant):
     q = 19
     g = (2e4, 5e3, 0.0)
@@ -174,6 +175,26 @@ def test_lbm_fp32_populations(rbf, cell, variant):
     _, om, _ = oracle.velocity_set(q)
     got = s.lbm_get_populations()
     assert rel_inf(got - om[:, None], want - om[:, None]) <= 1e-4
+
+
+@pytest.mark.parametrize("first,second", [(1, 6), (7, 0)])
+def test_lbm_layout_switch_mid_run(rbf, cell, first, second):
+    """Switching between schedules of the pairs and node-record layouts rewrites
+    the state; the run continues on the oracle's trajectory."""
+    q, g = 19, (2e4, 5e3, 0.0)
+    s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP64, g)
+    s.set_kernel_variant(first)
+    s.step(25)
+    mid = s.lbm_get_populations()
+    s.set_kernel_variant(second)
+    assert np.array_equal(s.lbm_get_populations(), mid)
+    s.step(35)
+    tm = oracle.tau_minus(0.8, 3.0 / 16.0)
+    f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
+    fn = oracle.lbm_run(f0, q, cell, idx, wk, 0.8, tm, u["g_lb"], 60)
+    want = oracle.lbm_collide(fn, q, 0.8, tm, u["g_lb"])
+    _, om, _ = oracle.velocity_set(q)
+    assert rel_inf(s.lbm_get_populations() - om[:, None], want - om[:, None]) <= 1e-9
 
 
 def test_permeability_and_drag_fp64(rbf, cell, orc_acm):
@@ -249,7 +270,7 @@ def test_autotune_keeps_state_and_parity(rbf, cell, orc_acm, solver):
         s.step(7)
         before = s.lbm_get_populations()
         times, chosen = s.autotune(10)
-        assert len(times) == 6 and chosen in times
+        assert len(times) == 8 and chosen in times
         assert np.array_equal(s.lbm_get_populations(), before)
         s.step(23)
         tm = oracle.tau_minus(0.8, 3.0 / 16.0)
