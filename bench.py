@@ -37,7 +37,7 @@ R, H_MIN, H_MAX, RAMP, SEED = 0.40, 0.008, 0.04, 0.2, 2
 N_L, Q, DX, TAU_P, MAGIC = 30, 19, 0.004, 0.8, 3.0 / 16.0
 KERNELS = {0: "k_lbm_step<float,19> (256)", 1: "k_lbm_step_pairs<float,19,5>", 2: "k_lbm_step<float,19> (128)",
            3: "k_lbm_step_pairs<float,19,3>", 4: "k_lbm_step_pairs<float,19,6>", 5: "k_lbm_step_pairs<float,19,2>",
-           6: "k_lbm_step_records<float,19,1> (256)", 7: "k_lbm_step_records<float,19,2> (128)"}
+           6: "k_lbm_step_records<float,19,4> (256)", 7: "k_lbm_step_records<float,19,5> (256)"}
 
 
 def workload():
@@ -295,7 +295,8 @@ def main():
     elt = 8 if args.precision == "fp64" else 4
     bpl = bytes_per_node_step(elt=elt) * n
     achieved = bpl / (per_launch_ms / 1e3) / 1e9
-    kname = KERNELS[chosen] if elt == 4 else KERNELS[chosen].replace("float", "double")
+    kname = KERNELS[chosen] if elt == 4 else (KERNELS[chosen].replace("float", "double")
+                                              .replace(",19,4>", ",19,2>").replace(",19,5>", ",19,3>"))
     cpu = None if (args.no_cpu_baseline or ws > 1) else oracle_baseline(case)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -208,8 +208,8 @@ int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classe
  * 0-5 keep the populations as the rest population plus interleaved opposite
  * pairs; 6 and 7 keep each node's q populations in one record of q rounded up
  * to a multiple of 4 values, read with 16-byte loads: 6 one node per thread,
- * 256-thread blocks; 7 the same with 128-thread blocks and the stencil loop
- * unrolled 2 deep.  Switching between the two layouts on an initialised LBM
+ * 256-thread blocks; 7 the same with registers capped so that five blocks fit
+ * on an SM.  Switching between the two layouts on an initialised LBM
  * context rewrites the state (one kernel launch); the populations, as
  * rbf_lbm_get_populations reports them, are unchanged. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);

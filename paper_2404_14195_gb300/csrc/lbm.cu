@@ -187,10 +187,12 @@ template <> struct Vec16<double> {
 // One thread per node on the node layout: each stencil column costs one index
 // load, (q-1)/2 coalesced 8-byte weight loads and lbm_rec_len(q) / 4 16-byte
 // loads of the neighbour's record (FP32 D3Q19: 5, against 9 pair gathers on the
-// pairs layout), U columns in flight.  Same arithmetic, in the same order, as
+// pairs layout).  MINB: blocks of 256 threads the compiler must fit on one SM,
+// i.e. a register cap (FP32: 4 -> 64 registers, no spills; 5 -> 48 registers, a
+// few spills, more warps in flight).  Same arithmetic, in the same order, as
 // k_lbm_step.
-template <typename T, int Q, int U>
-__global__ void __launch_bounds__(256) k_lbm_step_records(LbmArgs<T> a) {
+template <typename T, int Q, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
     using V = typename Vec2<T>::type;
     using W = Vec16<T>;
     using V16 = typename W::type;
@@ -208,8 +210,8 @@ __global__ void __launch_bounds__(256) k_lbm_step_records(LbmArgs<T> a) {
     T f[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) f[k] = (T)0;
-#pragma unroll U
-    for (int j = 0; j < n_l; ++j) {
+#pragma unroll 1
+    for (int j = 0; j < n_l; ++j) {  // not unrolled: keeps the register cap without spills
         const int q = __ldg(ip + (j << 5));
         T g[RL];
 #pragma unroll
@@ -445,9 +447,12 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
     case LBM_PAIR_PER_WARP_U3: k_lbm_step_pairs<T, Q, 3><<<slices, 32 * NP, 0, st>>>(a); break;
     case LBM_PAIR_PER_WARP_U6: k_lbm_step_pairs<T, Q, 6><<<slices, 32 * NP, 0, st>>>(a); break;
     case LBM_PAIR_PER_WARP_U2: k_lbm_step_pairs<T, Q, 2><<<slices, 32 * NP, 0, st>>>(a); break;
-    case LBM_RECORD_PER_THREAD: k_lbm_step_records<T, Q, 1><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a); break;
-    case LBM_RECORD_PER_THREAD_128_U2:
-        k_lbm_step_records<T, Q, 2><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a);
+    // register caps: FP32 64 / 48 (4 / 5 blocks per SM); FP64 128 / 80 (2 / 3 blocks)
+    case LBM_RECORD_PER_THREAD:
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+        break;
+    case LBM_RECORD_PER_THREAD_OCC:
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 5 : 3><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -30,12 +30,12 @@ double host_lattice_weight(int q, int k);
 // schedules of the fused step (same arithmetic, different thread mapping):
 // on the pairs layout, node per thread with 256 / 128 threads per block and
 // pair per warp with the stencil loop unrolled 5 / 3 / 6 / 2 deep; on the node
-// layout, node per thread with 256 threads (stencil loop not unrolled) and 128
-// threads (unrolled 2 deep)
+// layout, node per thread with 256 threads, registers as needed or capped for
+// five blocks per SM
 enum {
     LBM_NODE_PER_THREAD = 0, LBM_PAIR_PER_WARP = 1, LBM_NODE_PER_THREAD_128 = 2,
     LBM_PAIR_PER_WARP_U3 = 3, LBM_PAIR_PER_WARP_U6 = 4, LBM_PAIR_PER_WARP_U2 = 5,
-    LBM_RECORD_PER_THREAD = 6, LBM_RECORD_PER_THREAD_128_U2 = 7, LBM_N_SCHEDULES = 8
+    LBM_RECORD_PER_THREAD = 6, LBM_RECORD_PER_THREAD_OCC = 7, LBM_N_SCHEDULES = 8
 };
 __host__ __device__ constexpr int lbm_layout_of(int schedule) {
     return schedule >= LBM_RECORD_PER_THREAD ? LBM_LAYOUT_NODES : LBM_LAYOUT_PAIRS;
