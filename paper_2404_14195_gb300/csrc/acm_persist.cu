@@ -84,8 +84,9 @@ __device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool s
     T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
 #pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
-        const int q = ip[j << 5];
-        const T wx = wp[j << 5], wy = wp[(n_l + j) << 5], wz = wp[(2 * n_l + j) << 5], wl = wp[(3 * n_l + j) << 5];
+        const int q = __ldcs(ip + (j << 5));
+        const T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5));
+        const T wz = __ldcs(wp + ((2 * n_l + j) << 5)), wl = __ldcs(wp + ((3 * n_l + j) << 5));
         const T uq = c.u[q], vq = c.v[q], wq = c.w_[q];
         gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
         gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
@@ -125,8 +126,9 @@ __device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool 
     T div = 0;
 #pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
-        const int q = ip[j << 5];
-        div += wp[j << 5] * u[q] + wp[(n_l + j) << 5] * v[q] + wp[(2 * n_l + j) << 5] * w[q];
+        const int q = __ldcs(ip + (j << 5));
+        div += __ldcs(wp + (j << 5)) * u[q] + __ldcs(wp + ((n_l + j) << 5)) * v[q] +
+               __ldcs(wp + ((2 * n_l + j) << 5)) * w[q];
     }
     const T Ct = (T)C;
     if constexpr (CP) {
@@ -147,9 +149,9 @@ __device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
     const T *__restrict__ wp = c.wn + ((ls * n_l) << 5) + lane;
     T acc = 0;
 #pragma unroll 4
-    for (int j = 1; j < n_l; ++j) acc += wp[j << 5] * c.p[ip[j << 5]];
+    for (int j = 1; j < n_l; ++j) acc += __ldcs(wp + (j << 5)) * c.p[__ldcs(ip + (j << 5))];
     const int32_t wb = c.wall[b];
-    c.p[wb] = -acc / wp[0];
+    c.p[wb] = -acc / __ldcs(wp);
     if constexpr (CP) c.pl[wb] = (T)0;
 }
 
@@ -168,10 +170,10 @@ __device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
     T gx = 0, gy = 0, gz = 0;
 #pragma unroll 5
     for (int j = 0; j < n_l; ++j) {
-        const T pq = c.p[ip[j << 5]];
-        gx += wp[j << 5] * pq;
-        gy += wp[(n_l + j) << 5] * pq;
-        gz += wp[(2 * n_l + j) << 5] * pq;
+        const T pq = c.p[__ldcs(ip + (j << 5))];
+        gx += __ldcs(wp + (j << 5)) * pq;
+        gy += __ldcs(wp + ((n_l + j) << 5)) * pq;
+        gz += __ldcs(wp + ((2 * n_l + j) << 5)) * pq;
     }
     const T f = c.dt / c.rho;
     T un, vn, wn;
