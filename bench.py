@@ -592,8 +592,19 @@ def _mlp_train(args, rbf, local, dist, ws, peaks):
 
     wall, clk = _timed(work, local, dist)
     tmax = _max_over_ranks(wall, dist)
+    launches = m.launch_count() - l0
     fl = _mlp_flops_per_sample() * B * args.steps / tmax / 1e12
     peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+    # the per-layer schedule (one GEMM launch per layer and pass) on the same work, for comparison
+    m.set_fused(False)
+    m.train(args.warmup, B, 1e-3, 1)
+    holder2 = {}
+
+    def work2():
+        holder2["loss"] = m.train(args.steps, B, 1e-3, 1)
+
+    wall2, _ = _timed(work2, local, dist)
+    m.set_fused(True)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         th = om.init_params(1)
@@ -610,13 +621,16 @@ def _mlp_train(args, rbf, local, dist, ws, peaks):
         "unit": "samples/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 (fp32 accumulate, fp32 Adam)", "data": "synthetic random samples",
-        "config": {"workload": f"MLP 64-128x4-16 GELU, batch {B}, forward + backward + Adam per step (CUDA graph)",
-                   "batch": B, "parallelism": f"replicas x{ws}"},
+        "config": {"workload": f"MLP 64-128x4-16 GELU, batch {B}, forward + backward + Adam per step (CUDA graph): "
+                               f"fused tcgen05 forward and backward kernels",
+                   "batch": B, "parallelism": f"replicas x{ws}",
+                   "per_layer_schedule": {"samples_per_s": ws * B * args.steps / wall2,
+                                          "ms_per_step": 1e3 * wall2 / args.steps}},
         "roofline": {"bound": "tensor", "achieved": fl, "peak": peak, "unit": "TFLOP/s", "frac": fl / peak,
-                     "traffic": None, "kernel": "k_gemm (tcgen05) + epilogues, whole training step",
+                     "traffic": None, "kernel": "k_mlp_fwd + k_mlp_bwd (tcgen05), whole training step",
                      "flops_per_sample": _mlp_flops_per_sample(),
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
-        "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(m.launch_count() - l0), "clocks": clk,
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches), "clocks": clk,
         "final_loss": float(holder["loss"][-1]), "wall_s_timed": wall,
     }
 

@@ -328,6 +328,14 @@ int rbf_mlp_predict(rbf_mlp *mlp, int64_t n, const double *xyz, const float *rad
  * scale: 4 doubles (host). */
 int rbf_mlp_warm_start(rbf_mlp *mlp, rbf_ctx *ctx, const double *scale);
 int64_t rbf_mlp_launch_count(const rbf_mlp *mlp);
+/* Training-step schedule (rbf_mlp_train, rbf_mlp_gradient): 1 (default) two fused
+ * kernels per step, each CTA carrying 128-row tiles through all five layers with
+ * the weights resident in shared memory (forward, then backward with the weight
+ * and bias gradients added by vector reductions, so their summation order varies
+ * from run to run); 0 one tensor-core GEMM launch per layer and pass with
+ * split-batch weight gradients reduced in a fixed order.  Same rounding points in
+ * both. */
+int rbf_mlp_set_fused(rbf_mlp *mlp, int fused);
 
 /* Permeability exactly as rbf_permeability(m_p), for callers that cannot allocate
  * device memory at this point: for example code whose device memory is owned by

@@ -123,6 +123,7 @@ ABI = {
     "rbf_mlp_gradient": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
     "rbf_mlp_predict": (_I, [_P, _I64, _P, _P, _P, _P]),
     "rbf_mlp_warm_start": (_I, [_P, _P, _P]),
+    "rbf_mlp_set_fused": (_I, [_P, _I]),
     "rbf_mlp_launch_count": (_I64, [_P]),
 }
 
@@ -507,6 +508,11 @@ class Mlp:
         divided by for training, ones by default)."""
         sc = np.ascontiguousarray(np.broadcast_to(np.asarray(scale, np.float64), (4,)) * self.out_scale, np.float64)
         self._ck(self._L.rbf_mlp_warm_start(self._h, solver._h, _ptr(sc)))
+
+    def set_fused(self, fused: bool = True):
+        """Training-step schedule: fused forward/backward kernels (default) or one
+        GEMM launch per layer and pass."""
+        self._ck(self._L.rbf_mlp_set_fused(self._h, int(bool(fused))))
 
     def launch_count(self) -> int:
         return int(self._L.rbf_mlp_launch_count(self._h))

@@ -41,6 +41,14 @@ int64_t w_off(int l) {  // offset of W_l in the packed parameter vector
 }
 int64_t b_off(int l) { return w_off(l) + (int64_t)fan_out(l) * fan_in(l); }
 int64_t n_params_total() { return w_off(N_LAYERS); }
+__host__ __device__ constexpr int64_t w_off_c(int l) {  // w_off / b_off usable in device code
+    return l == 0 ? 0 : w_off_c(l - 1) + (int64_t)fan_out(l - 1) * fan_in(l - 1) + fan_out(l - 1);
+}
+__host__ __device__ constexpr int64_t b_off_c(int l) { return w_off_c(l) + (int64_t)fan_out(l) * fan_in(l); }
+
+// element offset of (r, k) in a K-major no-swizzle core-matrix operand with K columns:
+// 8 x 8 blocks of 128 bytes, adjacent along K (LBO = 128 B), row groups 16 K bytes apart
+__device__ __forceinline__ int cmo(int r, int k, int K) { return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7); }
 
 // ---- tcgen05 GEMM -------------------------------------------------------------------
 enum { EP_F32 = 0, EP_FWD = 1, EP_OUT = 2, EP_BWD = 3, EP_PRED = 4 };
@@ -75,6 +83,12 @@ __device__ __forceinline__ float gelu_f(float z) {
 __device__ __forceinline__ float gelu_prime_f(float z) {
     const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
+}
+// GELU and its derivative from one tanh (same expressions as gelu_f, gelu_prime_f)
+__device__ __forceinline__ void gelu_both(float z, float &h, float &g) {
+    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
+    h = 0.5f * z * (1.0f + t);
+    g = 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
 }
 
 // copy rows [r0, r0 + nrows) x cols [k0, k0 + kw) of a K-major BF16 matrix into the
@@ -302,6 +316,7 @@ __global__ void k_reduce_splits(const float *__restrict__ part, int ksplit, int 
 // Adam on the packed FP32 parameters, then the BF16 copies W_l [out][in] and W_l^T [in][out]
 struct BfPtrs {
     bf16 *W[N_LAYERS], *Wt[N_LAYERS];
+    bf16 *Wc[N_LAYERS], *Wtc[N_LAYERS];  // core-matrix layouts (K = fan_in / fan_out) of the fused kernels
 };
 __global__ void k_adam(int64_t np, float *theta, const float *grad, float *m, float *v, const int64_t *t_dev, float lr,
                        float b1, float b2, float eps, int update, BfPtrs bp) {
@@ -329,6 +344,8 @@ __global__ void k_adam(int64_t np, float *theta, const float *grad, float *m, fl
             const bf16 hb = __float2bfloat16(th);
             bp.W[l][q] = hb;
             bp.Wt[l][(int64_t)c * fan_out(l) + r] = hb;
+            bp.Wc[l][cmo(r, c, fan_in(l))] = hb;
+            bp.Wtc[l][cmo(c, r, fan_out(l))] = hb;
             return;
         }
         o += nw + fan_out(l);
@@ -363,6 +380,370 @@ __global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx,
     sdf[i] = (float)(sqrt(dx * dx + dy * dy + dz * dz) - r);
 }
 
+// ---- fused training step -------------------------------------------------------------
+// Two kernels per training step instead of one GEMM launch per layer and pass.  A CTA
+// owns 128-row tiles of the batch (row = TMEM lane).
+//
+//  k_mlp_fwd: draws the tile's samples, computes their features, and runs the five
+//    layers back to back: A operand = the tile's activations in shared memory, B =
+//    the layer's weights (all five bulk-copied into shared memory once per CTA),
+//    accumulator in TMEM; the epilogue (bias, GELU, GELU') writes the next layer's A
+//    operand in place and keeps H_l, GELU'(Z_l) and the output error dY in global
+//    memory for the backward kernel.
+//  k_mlp_bwd: for l = 5..1, from dZ_l (rows in shared memory, normal and
+//    transposed): dW_l = dZ_l^T H_{l-1} and dH_{l-1} = dZ_l W_l as two tcgen05 MMA
+//    chains (W_l^T resident in shared memory), dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1});
+//    the tile's dW and db are added into the gradient with vector reductions.
+//
+// Operands are K-major BF16 in the no-swizzle core-matrix layout with the whole K
+// in one buffer: element (r, k) of an R x K operand at byte
+// ((r/8) (K/8) + k/8) 128 + (r%8) 16 + (k%8) 2, so LBO = 128 B and SBO = 16 K B.
+// The rounding points are those of the per-layer path: BF16 features, activations,
+// GELU' and back-propagated errors, FP32 accumulation.
+constexpr int FW_WBYTES = 2 * (N_H * N_IN + 3 * N_H * N_H + N_OUT_PAD * N_H);  // W_1..W_5
+constexpr int FB_WBYTES = 2 * (3 * N_H * N_H + N_H * N_OUT_PAD);               // W_2^T..W_5^T
+constexpr int TILE_BYTES = 2 * 128 * 128;
+constexpr size_t FW_SMEM = FW_WBYTES + TILE_BYTES + 64 + 1024;
+constexpr size_t FB_SMEM = FB_WBYTES + 3 * TILE_BYTES + 4 * 128 * 4 + 64 + 1024;
+
+struct FusedArgs {
+    int B;                       // rows, a multiple of 128
+    int64_t n;                   // samples in the data
+    const double *xyz;
+    const float *rad, *sdf, *tgt;
+    const int64_t *idx;          // explicit sample indices, or null: counter-based draws
+    uint64_t seed;
+    const int64_t *step_dev;
+    const bf16 *Wc[N_LAYERS];    // W_l [fan_out][fan_in], core layout, K = fan_in
+    const bf16 *Wtc[N_LAYERS];   // W_l^T [fan_in][fan_out], core layout, K = fan_out (l >= 1)
+    const float *theta;          // FP32 masters (biases)
+    bf16 *X;                     // [B][64]
+    bf16 *H[4], *G[4];           // [B][128]
+    bf16 *dY;                    // [B][16]
+    float *loss, *grad;
+    float gscale;
+    int32_t *err;
+};
+
+// this thread's shared-memory stores -> visible to the tensor cores, then a CTA barrier
+__device__ __forceinline__ void smem_to_mma_sync() {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// D (TMEM) = A B^T over K, both operands K-major in shared memory (A: K_A = K columns)
+__device__ __forceinline__ void mma_chain(uint32_t d, const bf16 *A, const bf16 *Bm, int K, uint32_t idesc) {
+    for (int kk = 0; kk < (K >> 4); ++kk) {
+        const uint64_t da = tc::smem_desc(reinterpret_cast<const uint8_t *>(A) + kk * 256, 128, 16 * K);
+        const uint64_t db = tc::smem_desc(reinterpret_cast<const uint8_t *>(Bm) + kk * 256, 128, 16 * K);
+        tc::mma_bf16(d, da, db, idesc, kk > 0 ? 1u : 0u);
+    }
+}
+
+// 8 BF16 values as one 16-byte word
+__device__ __forceinline__ uint4 pack8(const bf16 *v) { return *reinterpret_cast<const uint4 *>(v); }
+
+// Both kernels run 256 threads: thread t serves row t % 128 of the tile (TMEM lane
+// t % 128, reachable by warps w and w + 4) and half h = t / 128 of each layer's
+// columns, so two warps per scheduler share the epilogue math.
+__global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    bf16 *sW[N_LAYERS];
+    uint8_t *p = smem;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        sW[l] = reinterpret_cast<bf16 *>(p);
+        p += 2 * fan_out(l) * fan_in(l);
+    }
+    bf16 *act = reinterpret_cast<bf16 *>(p);
+    p += TILE_BYTES;
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int row = t & 127, half = t >> 7;
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (t == 0) {
+        tc::mbar_init(wbar, 1);
+        tc::mbar_init(mbar, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot, tlane = (uint32_t)((warp & 3) * 32) << 16;
+    if (t == 0) {
+        tc::mbar_arrive_expect_tx(wbar, FW_WBYTES);
+        for (int l = 0; l < N_LAYERS; ++l) tc::bulk_copy_g2s(sW[l], f.Wc[l], 2 * fan_out(l) * fan_in(l), wbar);
+    }
+    bool ok = tc::mbar_wait(wbar, 0, WAIT_NS);
+    uint32_t phase = 0;
+    float lsum = 0.0f;
+    for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
+        const int64_t r = (int64_t)tile * 128 + row;
+        int64_t s;
+        if (f.idx) s = f.idx[r];
+        else {
+            const uint64_t c = f.seed * (1ull << 32) + (uint64_t)(*f.step_dev) * (uint64_t)f.B + (uint64_t)r;
+            s = (int64_t)(splitmix64(c) % (uint64_t)f.n);
+        }
+        {   // features of sample s (half h: wave vectors 8h .. 8h + 7; half 0 also r and
+            // phi_sdf): the sines and cosines of k_features, evaluated in FP32 on the
+            // coordinates reduced to [0, 1) (periodic, so exact up to float rounding,
+            // ~1e-7, far below the BF16 resolution the features are stored at)
+            const double x = f.xyz[3 * s], y = f.xyz[3 * s + 1], z = f.xyz[3 * s + 2];
+            const float xf = (float)(x - floor(x)), yf = (float)(y - floor(y)), zf = (float)(z - floor(z));
+            __align__(16) bf16 part[32];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int j = 8 * half + jj;
+                float sn, cs;
+                sincospif(2.0f * ((float)c_waves[j][0] * xf + (float)c_waves[j][1] * yf + (float)c_waves[j][2] * zf), &sn,
+                          &cs);
+                part[2 * jj] = __float2bfloat16(sn);
+                part[2 * jj + 1] = __float2bfloat16(cs);
+            }
+#pragma unroll
+            for (int j = 16; j < 32; ++j) part[j] = __float2bfloat16(0.0f);
+            if (half == 0) {
+                part[16] = __float2bfloat16(f.rad[s]);  // columns 32, 33 of the row
+                part[17] = __float2bfloat16(f.sdf[s]);
+            }
+            // half 0 owns columns 0..15 and 32..47 (r, phi_sdf, zeros), half 1 columns
+            // 16..31 and 48..63 (zeros): each written as two 16-column pieces
+            const int cA = 16 * half, cB = 32 + 16 * half;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const uint4 wA = pack8(part + 8 * k), wB = pack8(part + 16 + 8 * k);
+                *reinterpret_cast<uint4 *>(act + cmo(row, cA + 8 * k, N_IN)) = wA;
+                *reinterpret_cast<uint4 *>(act + cmo(row, cB + 8 * k, N_IN)) = wB;
+                reinterpret_cast<uint4 *>(f.X + r * N_IN)[(cA >> 3) + k] = wA;
+                reinterpret_cast<uint4 *>(f.X + r * N_IN)[(cB >> 3) + k] = wB;
+            }
+        }
+        float tg[N_OUT];
+#pragma unroll
+        for (int c = 0; c < N_OUT; ++c) tg[c] = half ? 0.0f : f.tgt[s * N_OUT + c];
+        for (int l = 0; l < N_LAYERS && ok; ++l) {
+            const int fi = fan_in(l), fo = fan_out(l);
+            smem_to_mma_sync();
+            if (t == 0) {
+                mma_chain(tmem, act, sW[l], fi, tc::idesc_bf16_f32(128, fo));
+                tc::mma_commit(mbar);
+            }
+            ok = tc::mbar_wait(mbar, phase, WAIT_NS);
+            phase ^= 1;
+            if (!ok) break;
+            tc::fence_after_sync();
+            const float *bias = f.theta + b_off_c(l);
+            if (l < N_LAYERS - 1) {
+                for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
+                    __align__(16) bf16 hv[16];
+                    __align__(16) bf16 gv[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float h, g;
+                        gelu_both(v[i] + bias[c0 + i], h, g);
+                        hv[i] = __float2bfloat16(h);
+                        gv[i] = __float2bfloat16(g);
+                    }
+                    *reinterpret_cast<uint4 *>(act + cmo(row, c0, N_H)) = pack8(hv);
+                    *reinterpret_cast<uint4 *>(act + cmo(row, c0 + 8, N_H)) = pack8(hv + 8);
+                    uint4 *hd = reinterpret_cast<uint4 *>(f.H[l] + r * N_H + c0);
+                    uint4 *gd = reinterpret_cast<uint4 *>(f.G[l] + r * N_H + c0);
+                    hd[0] = pack8(hv); hd[1] = pack8(hv + 8);
+                    gd[0] = pack8(gv); gd[1] = pack8(gv + 8);
+                }
+            } else if (half == 0) {
+                float v[16];
+                tc::tmem_ld16(tmem + tlane, v);
+                __align__(16) bf16 dv[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float dy = 0.0f;
+                    if (c < N_OUT) {
+                        const float e = v[c] + bias[c] - tg[c];
+                        lsum += e * e;
+                        dy = f.gscale * e;
+                    }
+                    dv[c] = __float2bfloat16(dy);
+                }
+                uint4 *dd = reinterpret_cast<uint4 *>(f.dY + r * N_OUT_PAD);
+                dd[0] = pack8(dv); dd[1] = pack8(dv + 8);
+            }
+            tc::fence_before_sync();
+        }
+    }
+    if (!ok) {  // a wait ran out: report, give the outstanding work one more bounded wait
+        if (t == 0) atomicExch(f.err, 1);
+        tc::mbar_wait(mbar, phase, WAIT_NS);
+    }
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    if (lane == 0 && lsum != 0.0f) atomicAdd(f.loss, lsum);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+__global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    bf16 *sWt[N_LAYERS] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint8_t *p = smem;
+    for (int l = 1; l < N_LAYERS; ++l) {
+        sWt[l] = reinterpret_cast<bf16 *>(p);
+        p += 2 * fan_out(l) * fan_in(l);
+    }
+    bf16 *An = reinterpret_cast<bf16 *>(p);                  // dZ_l [128 rows][fan_out], K = fan_out
+    bf16 *At = reinterpret_cast<bf16 *>(p + TILE_BYTES);     // dZ_l^T [fan_out][128 rows], K = 128
+    bf16 *Bt = reinterpret_cast<bf16 *>(p + 2 * TILE_BYTES); // H_{l-1}^T [fan_in][128 rows], K = 128
+    p += 3 * TILE_BYTES;
+    float *colsum = reinterpret_cast<float *>(p);             // [4 row groups][128 columns]
+    p += 4 * 128 * 4;
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int row = t & 127, half = t >> 7, wq = warp & 3;
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 256);
+        tc::tmem_relinquish();
+    }
+    if (t == 0) {
+        tc::mbar_init(wbar, 1);
+        tc::mbar_init(mbar, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot, tlane = (uint32_t)(wq * 32) << 16;
+    if (t == 0) {
+        tc::mbar_arrive_expect_tx(wbar, FB_WBYTES);
+        for (int l = 1; l < N_LAYERS; ++l) tc::bulk_copy_g2s(sWt[l], f.Wtc[l], 2 * fan_out(l) * fan_in(l), wbar);
+    }
+    bool ok = tc::mbar_wait(wbar, 0, WAIT_NS);
+    uint32_t phase = 0;
+    // column sums of this thread's dz values over its warp's 32 rows, into colsum[wq][c0 ..]
+    auto colsum16 = [&](const float *dz, int c0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float sv = dz[i];
+            for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+            if (lane == 0) colsum[wq * 128 + c0 + i] = sv;
+        }
+    };
+    for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
+        const int64_t r = (int64_t)tile * 128 + row;
+        if (half == 0) {  // dZ_5 = dY: normal (K = 16) and transposed rows, and its column sums (db_5)
+            __align__(16) bf16 dv[16];
+            const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + r * N_OUT_PAD);
+            *reinterpret_cast<uint4 *>(dv) = src[0];
+            *reinterpret_cast<uint4 *>(dv + 8) = src[1];
+            *reinterpret_cast<uint4 *>(An + cmo(row, 0, N_OUT_PAD)) = pack8(dv);
+            *reinterpret_cast<uint4 *>(An + cmo(row, 8, N_OUT_PAD)) = pack8(dv + 8);
+            float dz[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                At[cmo(c, row, 128)] = dv[c];
+                dz[c] = __bfloat162float(dv[c]);
+            }
+            colsum16(dz, 0);
+        }
+        __syncthreads();
+        if (t < N_OUT_PAD) {
+            const float sv = colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
+            if (sv != 0.0f) atomicAdd(f.grad + b_off_c(N_LAYERS - 1) + t, sv);
+        }
+        for (int l = N_LAYERS - 1; l >= 0 && ok; --l) {
+            const int fi = fan_in(l), fo = fan_out(l), hw = fi >> 1;
+            {   // B_T = H_{l-1}^T (X^T for the first layer); half h: columns [h fi/2, (h+1) fi/2)
+                const bf16 *hin = l > 0 ? f.H[l - 1] + r * N_H : f.X + r * N_IN;
+                for (int c = hw * half; c < hw * half + hw; c += 8) {
+                    __align__(16) bf16 hv[8];
+                    *reinterpret_cast<uint4 *>(hv) = reinterpret_cast<const uint4 *>(hin)[c >> 3];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) Bt[cmo(c + i, row, 128)] = hv[i];
+                }
+            }
+            smem_to_mma_sync();
+            if (t == 0) {
+                if (l == N_LAYERS - 1)  // dW_5^T [128 in][16 out] = H_4^T dZ_5
+                    mma_chain(tmem + 128, Bt, At, 128, tc::idesc_bf16_f32(128, N_OUT_PAD));
+                else                    // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}
+                    mma_chain(tmem + 128, At, Bt, 128, tc::idesc_bf16_f32(128, fi));
+                if (l > 0)              // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
+                    mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
+                tc::mma_commit(mbar);
+            }
+            ok = tc::mbar_wait(mbar, phase, WAIT_NS);
+            phase ^= 1;
+            if (!ok) break;
+            tc::fence_after_sync();
+            if (l == N_LAYERS - 1) {  // lane = input unit: dW_5[o][row], o < 16
+                if (half == 0) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + tlane + 128, v);
+#pragma unroll
+                    for (int o = 0; o < N_OUT_PAD; ++o)
+                        if (v[o] != 0.0f) atomicAdd(f.grad + w_off_c(l) + o * N_H + row, v[o]);
+                }
+            } else {                  // lane = output unit: row `row` of dW_l, columns of this half
+                float *gw = f.grad + w_off_c(l) + (int64_t)row * fi;
+                for (int c0 = hw * half; c0 < hw * half + hw; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + tlane + 128 + (uint32_t)c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) tc::red_add_v4(gw + c0 + i, v[i], v[i + 1], v[i + 2], v[i + 3]);
+                }
+            }
+            if (l > 0) {  // dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1}); its column sums are db_{l-1}
+                const bf16 *gr = f.G[l - 1] + r * N_H;
+                for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
+                    __align__(16) bf16 gv[16];
+                    *reinterpret_cast<uint4 *>(gv) = reinterpret_cast<const uint4 *>(gr + c0)[0];
+                    *reinterpret_cast<uint4 *>(gv + 8) = reinterpret_cast<const uint4 *>(gr + c0)[1];
+                    __align__(16) bf16 dv[16];
+                    float dz[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        dv[i] = __float2bfloat16(v[i] * __bfloat162float(gv[i]));
+                        dz[i] = __bfloat162float(dv[i]);
+                        At[cmo(c0 + i, row, 128)] = dv[i];
+                    }
+                    *reinterpret_cast<uint4 *>(An + cmo(row, c0, N_H)) = pack8(dv);
+                    *reinterpret_cast<uint4 *>(An + cmo(row, c0 + 8, N_H)) = pack8(dv + 8);
+                    colsum16(dz, c0);
+                }
+                __syncthreads();
+                if (t < N_H) {
+                    const float sv = colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
+                    if (sv != 0.0f) atomicAdd(f.grad + b_off_c(l - 1) + t, sv);
+                }
+            }
+            tc::fence_before_sync();
+        }
+    }
+    if (!ok) {
+        if (t == 0) atomicExch(f.err, 1);
+        tc::mbar_wait(mbar, phase, WAIT_NS);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+cudaError_t fused_set_smem() {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM);
+    return e;
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -374,7 +755,9 @@ struct rbf_mlp {
     std::string err;
     int64_t launches = 0;
     DevArr<float> theta, m, v, grad;
-    DevArr<bf16> W[N_LAYERS], Wt[N_LAYERS];
+    DevArr<bf16> W[N_LAYERS], Wt[N_LAYERS], Wc[N_LAYERS], Wtc[N_LAYERS];
+    int nsm = 0;
+    bool fused = true;  // training step: fused forward and backward kernels (else one GEMM per layer and pass)
     DevArr<int64_t> counters;  // [0] Adam step t, [1] batch draw step
     // training data
     int64_t nd = 0;
@@ -424,6 +807,8 @@ BfPtrs bf_ptrs(rbf_mlp *mm) {
     for (int l = 0; l < N_LAYERS; ++l) {
         b.W[l] = mm->W[l].p;
         b.Wt[l] = mm->Wt[l].p;
+        b.Wc[l] = mm->Wc[l].p;
+        b.Wtc[l] = mm->Wtc[l].p;
     }
     return b;
 }
@@ -546,15 +931,39 @@ cudaError_t enqueue_backward(rbf_mlp *mm, int B) {
     return cudaGetLastError();
 }
 
+// the fused forward and backward kernels of one training step on B rows
+cudaError_t enqueue_fused(rbf_mlp *mm, int B, uint64_t seed, const int64_t *explicit_idx) {
+    FusedArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.B = B; f.n = mm->nd; f.xyz = mm->dxyz.p; f.rad = mm->drad.p; f.sdf = mm->dsdf.p; f.tgt = mm->dtgt.p;
+    f.idx = explicit_idx; f.seed = seed; f.step_dev = mm->counters.p + 1;
+    for (int l = 0; l < N_LAYERS; ++l) { f.Wc[l] = mm->Wc[l].p; f.Wtc[l] = mm->Wtc[l].p; }
+    f.theta = mm->theta.p; f.X = mm->X.p;
+    for (int l = 0; l < 4; ++l) { f.H[l] = mm->H[l].p; f.G[l] = mm->G[l].p; }
+    f.dY = mm->dY.p; f.loss = mm->loss.p; f.grad = mm->grad.p;
+    f.gscale = 2.0f / ((float)B * N_OUT);
+    f.err = mm->errflag.p;
+    const unsigned grid = (unsigned)std::min(B / 128, std::max(mm->nsm, 1));
+    k_mlp_fwd<<<grid, 256, FW_SMEM, mm->st>>>(f);
+    k_mlp_bwd<<<grid, 256, FB_SMEM, mm->st>>>(f);
+    mm->launches += 2;
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_train_step(rbf_mlp *mm, int B, uint64_t seed, float lr, const int64_t *explicit_idx, bool update) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(mm->grad.p, 0, mm->grad.n * sizeof(float), mm->st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(mm->loss.p, 0, sizeof(float), mm->st)) != cudaSuccess) return e;
-    k_features<<<(B + 127) / 128, 128, 0, mm->st>>>(B, mm->nd, mm->dxyz.p, mm->drad.p, mm->dsdf.p, mm->dtgt.p,
-                                                    explicit_idx, seed, mm->counters.p + 1, mm->X.p, mm->Xt.p, B, mm->T.p);
-    ++mm->launches;
-    if ((e = enqueue_forward(mm, B, B, true)) != cudaSuccess) return e;
-    if ((e = enqueue_backward(mm, B)) != cudaSuccess) return e;
+    if (mm->fused) {
+        if ((e = enqueue_fused(mm, B, seed, explicit_idx)) != cudaSuccess) return e;
+    } else {
+        k_features<<<(B + 127) / 128, 128, 0, mm->st>>>(B, mm->nd, mm->dxyz.p, mm->drad.p, mm->dsdf.p, mm->dtgt.p,
+                                                        explicit_idx, seed, mm->counters.p + 1, mm->X.p, mm->Xt.p, B,
+                                                        mm->T.p);
+        ++mm->launches;
+        if ((e = enqueue_forward(mm, B, B, true)) != cudaSuccess) return e;
+        if ((e = enqueue_backward(mm, B)) != cudaSuccess) return e;
+    }
     if (update) {
         const int64_t np = n_params_total();
         k_adam<<<(unsigned)((np + 255) / 256), 256, 0, mm->st>>>(np, mm->theta.p, mm->grad.p, mm->m.p, mm->v.p,
@@ -595,10 +1004,14 @@ int rbf_mlp_create(rbf_mlp **out, int device, void *stream) {
     const int64_t np = n_params_total();
     bool ok = mm->theta.alloc(np) == cudaSuccess && mm->m.alloc(np) == cudaSuccess && mm->v.alloc(np) == cudaSuccess &&
               mm->grad.alloc(np) == cudaSuccess && mm->counters.alloc(2) == cudaSuccess &&
-              mm->loss.alloc(1) == cudaSuccess && mm->errflag.alloc(1) == cudaSuccess && gemm_set_smem() == cudaSuccess;
+              mm->loss.alloc(1) == cudaSuccess && mm->errflag.alloc(1) == cudaSuccess && gemm_set_smem() == cudaSuccess &&
+              fused_set_smem() == cudaSuccess &&
+              cudaDeviceGetAttribute(&mm->nsm, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     for (int l = 0; l < N_LAYERS && ok; ++l)
         ok = mm->W[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess &&
-             mm->Wt[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess;
+             mm->Wt[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess &&
+             mm->Wc[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess &&
+             mm->Wtc[l].alloc((size_t)fan_out(l) * fan_in(l)) == cudaSuccess;
     if (!ok) { rbf_mlp_destroy(mm); return RBF_ECUDA; }
     cudaMemsetAsync(mm->theta.p, 0, np * sizeof(float), mm->st);
     cudaMemsetAsync(mm->m.p, 0, np * sizeof(float), mm->st);
@@ -710,7 +1123,7 @@ int rbf_mlp_train(rbf_mlp *mm, int steps, int batch, double lr, uint64_t seed, f
     }
     for (int s = 0; s < steps; ++s) {
         MCK(cudaGraphLaunch(mm->gexec, mm->st));
-        mm->launches += 4 + 5 + 14 + 2;
+        mm->launches += mm->fused ? 2 + 2 : 1 + 5 + 14 + 2;
         if (loss_hist) MCK(cudaMemcpyAsync(loss_hist + s, mm->loss.p, sizeof(float), cudaMemcpyDeviceToHost, mm->st));
     }
     rc = check_err(mm);
@@ -805,5 +1218,17 @@ int rbf_mlp_warm_start(rbf_mlp *mm, rbf_ctx *ctx, const double *scale) {
 }
 
 int64_t rbf_mlp_launch_count(const rbf_mlp *mm) { return mm ? mm->launches : -1; }
+
+int rbf_mlp_set_fused(rbf_mlp *mm, int fused) {
+    if (!mm) return RBF_EINVAL;
+    MDevGuard dg(mm->device);
+    if (mm->st) MCK(cudaStreamSynchronize(mm->st));
+    if (mm->gexec) {
+        cudaGraphExecDestroy(mm->gexec);
+        mm->gexec = nullptr;
+    }
+    mm->fused = fused != 0;
+    return RBF_OK;
+}
 
 }  // extern "C"

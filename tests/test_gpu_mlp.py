@@ -8,7 +8,9 @@ oracle in oracle/mlp.py.
   norm-wise per layer (BF16 activations and back-propagated errors);
 * Adam: the first updates from the same parameters and batches agree with the
   oracle's to 5 % of the step size on parameters with a clear gradient;
-* training reduces the loss; the warm start writes the prediction into the solver.
+* training reduces the loss; the warm start writes the prediction into the solver;
+* the fused training kernels and the per-layer GEMM path give the same loss and
+  gradient (same rounding points, different summation order).
 """
 import numpy as np
 import pytest
@@ -134,3 +136,33 @@ def test_training_reduces_loss(rbf):
     assert hist[-20:].mean() < 0.2 * hist[:5].mean()
     pred = m.predict(xyz[:500], r[:500], sdf[:500])
     assert np.mean((pred - T[:500]) ** 2) < 0.2 * np.mean(T[:500] ** 2)
+
+
+def test_fused_and_per_layer_training_paths_agree(rbf):
+    theta = om.init_params(13).astype(np.float32)
+    xyz, r, sdf, X, T = _data(3000, seed=4)
+    idx = (np.arange(512, dtype=np.int64) * 11) % 3000
+    out = {}
+    for fused in (True, False):
+        m = rbf.Mlp(0)
+        m.set_fused(fused)
+        m.set_params(theta)
+        m.set_data(xyz, r, sdf, T)
+        out[fused] = m.gradient(idx)
+    (g1, l1), (g0, l0) = out[True], out[False]
+    assert abs(l1 - l0) <= 1e-5 * l0
+    o = 0
+    for fo, fi in om.param_sizes():
+        for sl in (slice(o, o + fo * fi), slice(o + fo * fi, o + fo * fi + fo)):
+            scale = np.abs(g0[sl]).max()
+            assert np.abs(g1[sl] - g0[sl]).max() <= 1e-3 * scale + 1e-12, (fo, fi)
+        o += fo * fi + fo
+    # several training steps of both schedules from the same start stay together
+    hist = {}
+    for fused in (True, False):
+        m = rbf.Mlp(0)
+        m.set_fused(fused)
+        m.set_params(theta)
+        m.set_data(xyz, r, sdf, T)
+        hist[fused] = m.train(20, 256, 1e-3, 3)
+    assert np.allclose(hist[True], hist[False], rtol=2e-3)
