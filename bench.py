@@ -256,11 +256,8 @@ def main():
         wall = time.perf_counter() - t0
         barrier()
     launches = s.launch_count() - l0
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax_ms = float(t.item())
-    value = ws * n * args.steps / (tmax_ms / 1e3)
+    tmax_ms = _max_over_ranks(total_ms, dist)
+    value = whole_job_rate(n * args.steps, ws, tmax_ms / 1e3)
 
     # per-launch kernel time with event pairs (eager launches, after the timed region)
     prof_ms = float(s.profile_steps(200)[0])
@@ -282,10 +279,7 @@ def main():
         out_host[:] = s.get_fields()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = ws * n * args.e2e_steps / float(e2e_t.item())
+    e2e_val = whole_job_rate(n * args.e2e_steps, ws, _max_over_ranks(e2e_s, dist))
 
     if rank != 0:
         dist.destroy_process_group()
@@ -420,11 +414,22 @@ def run_workload(args):
 
 
 def _max_over_ranks(x, dist):
+    """The largest x over all ranks (the whole job's time is its slowest rank's);
+    the reduction runs on the GPU under NCCL, on the host under gloo."""
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist is None or dist.get_backend() == "nccl" else "cpu"
+    if dist is None and not torch.cuda.is_available():
+        dev = "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world_size, seconds_max):
+    """Weak-scaling throughput: every rank processes units_per_rank units (its own
+    replica), the job takes the slowest rank's time."""
+    return world_size * units_per_rank / seconds_max
 
 
 def _acm_config4(args, rbf, local, dist, ws, peaks):
@@ -479,7 +484,7 @@ def _acm_config4(args, rbf, local, dist, ws, peaks):
     if not args.no_cpu_baseline and ws == 1:
         cpu = _oracle_acm_baseline(case, c)
     return {
-        "metric": "node-steps/s (ACM steps, config 4)", "value": ws * n * args.steps / (tmax / 1e3), "unit": UNIT,
+        "metric": "node-steps/s (ACM steps, config 4)", "value": whole_job_rate(n * args.steps, ws, tmax / 1e3), "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp32c": "f32 (compensated state)", "fp64": "f64"}[args.precision],
@@ -545,7 +550,8 @@ def _batch_config3(args, rbf, local, dist, ws, peaks, cells):
     gbs = byts * args.steps / tmax / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     return {
-        "metric": "node-steps/s (batched ACM steps, config 3)", "value": ws * n_tot * args.steps / tmax, "unit": UNIT,
+        "metric": "node-steps/s (batched ACM steps, config 3)", "value": whole_job_rate(n_tot * args.steps, ws, tmax),
+        "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp32c": "f32 (compensated state)", "fp64": "f64"}[args.precision],

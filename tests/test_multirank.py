@@ -1,0 +1,53 @@
+"""The multi-rank path of bench.py on the host (no GPU): two gloo ranks launched
+as torchrun would launch them (RANK / WORLD_SIZE / MASTER_ADDR in the
+environment).  Every rank times its own replica; the job's time is the slowest
+rank's (max over ranks) and its throughput the units of all ranks over that
+time (weak scaling, no collective on the data path)."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    ws, r, local = bench.dist_env()
+    assert (ws, r, local) == (world, rank, rank)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    seconds = [0.8, 1.25][rank]  # rank 1 is the slow one
+    tmax = bench._max_over_ranks(seconds, dist)
+    rate = bench.whole_job_rate(1000, ws, tmax)
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(f"{tmax} {rate}\n")
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_the_slowest(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for rank in (0, 1):
+        tmax, rate = map(float, open(tmp_path / f"rank{rank}.txt").read().split())
+        assert tmax == 1.25
+        assert abs(rate - 2 * 1000 / 1.25) < 1e-9
+
+
+def test_single_process_needs_no_collective():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._max_over_ranks(3.5, None) == 3.5
+    assert bench.whole_job_rate(10, 1, 2.0) == 5.0
