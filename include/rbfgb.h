@@ -232,16 +232,20 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
 
 /* Autotuner of the persistent ACM driver (rbf_solve): time 256, 128, 64 and 32
  * threads per block (one 32-node slice per warp; the grid is as many blocks as
- * cover the slices, at most the co-resident count) over trial_steps steps each,
- * CUDA events around the cooperative launch, and keep the fastest for this
- * context's later rbf_solve calls.  Fields and step parity are saved before and
- * restored after the trials.  ACM contexts only; 2 <= trial_steps <= 20000.
- * rep->code[c] is the block size of candidate c. */
+ * cover the slices, at most the co-resident count, synchronised by a software
+ * grid barrier) and, where the device can place them, one thread-block cluster
+ * of 16 or 8 CTAs of 256 threads synchronised by the hardware cluster barrier
+ * (codes -16, -8; for small cells), over trial_steps steps each, CUDA events
+ * around the launch, and keep the fastest for this context's later rbf_solve
+ * calls.  Fields and step parity are saved before and restored after the trials.
+ * ACM contexts only; 2 <= trial_steps <= 20000.  rep->code[c] is the code of
+ * candidate c. */
 int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
-/* Threads per block of the persistent ACM driver for this context (32, 64, 128
- * or 256; default 256).  A batch launches with its first cell's setting.  The
- * block size changes only the order of the FP64 residual partial sums, never
- * the fields. */
+/* Schedule of the persistent ACM driver for this context: 32, 64, 128 or 256
+ * threads per block of a cooperative grid (default 256), or -8 / -16 for one
+ * cluster of 8 / 16 CTAs of 256 threads.  A batch launches with its first cell's
+ * setting.  The schedule changes only the order of the FP64 residual partial
+ * sums, never the fields. */
 int rbf_set_persistent_block(rbf_ctx *ctx, int block);
 
 /* Number of kernel launches issued by this context since creation. */

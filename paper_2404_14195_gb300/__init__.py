@@ -322,7 +322,8 @@ class Solver:
         return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
 
     def set_persistent_block(self, block: int):
-        """Threads per block of the persistent ACM driver (32, 64, 128, 256)."""
+        """Persistent ACM driver schedule: threads per block of a cooperative grid
+        (32, 64, 128, 256) or -8 / -16 for one cluster of 8 / 16 CTAs."""
         self._ck(self._L.rbf_set_persistent_block(self._h, int(block)))
 
     def autotune_persistent(self, trial_steps: int = 200):

@@ -19,6 +19,8 @@
 // CP = true is the compensated FP32 state of acm.cu (hi + lo pairs, comp_add
 // updates, gathers of the hi words); its residual differences include the low
 // words.
+#include <cstring>
+
 #include "acm_persist.cuh"
 #include "acm.cuh"
 #include "tc.cuh"
@@ -191,7 +193,19 @@ __device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
     return (double)sqrt(un * un + vn * vn + wn * wn);
 }
 
-template <typename T, bool CP>
+// every thread of every CTA of the cluster arrives (release) and waits (acquire):
+// the hardware barrier of a thread-block cluster, no spinning on memory
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CL = false: a cooperative grid synchronised by grid_barrier (any number of
+// co-resident blocks); CL = true: one thread-block cluster (8 or 16 CTAs)
+// synchronised by the cluster's hardware barrier, for small cells where the
+// software barrier's latency dominates a step.  Every block of a cluster takes the
+// same branches at every barrier (the done flags change only before a barrier and
+// the cluster barrier cannot time out), so none is left waiting.
+template <typename T, bool CP, bool CL>
 __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__restrict__ cells, PersistCtl ctl) {
     __shared__ double racc[PERSIST_MAX_CELLS][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,11 +213,19 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
     const int64_t wstride = (int64_t)gridDim.x * wpb;
     const int64_t w0 = (int64_t)blockIdx.x * wpb + warp;
     const unsigned nblocks = gridDim.x;
+    auto grid_barrier = [&](unsigned *count, unsigned *gen, unsigned nb, int32_t *err) -> bool {
+        if constexpr (CL) {
+            cluster_barrier();
+            return true;
+        } else {
+            return rbf::grid_barrier(count, gen, nb, err);
+        }
+    };
     for (int64_t step = 0; step < ctl.max_steps; ++step) {
         // every block sees the same done flags here (they change only before a barrier)
         bool any = false;
         for (int c = 0; c < ctl.ncells; ++c) any |= !((volatile int32_t *)ctl.done)[c];
-        if (!any || *(volatile int32_t *)ctl.err) break;
+        if (!any || (!CL && *(volatile int32_t *)ctl.err)) break;
         const bool check = ((step + 1) % ctl.check_every == 0) || (step + 1 == ctl.max_steps);
         for (int64_t s = w0; s < ctl.nslices; s += wstride) {
             const int2 sl = ctl.slices[s];
@@ -315,8 +337,55 @@ cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl
                                   bool cp, cudaStream_t st) {
     if (!persist_block_ok(block) || nblocks < 1) return cudaErrorInvalidValue;
     void *args[] = {(void *)&cells_dev, (void *)&ctl};
-    const void *fn = cp ? (const void *)k_acm_persistent<T, true> : (const void *)k_acm_persistent<T, false>;
+    const void *fn = cp ? (const void *)k_acm_persistent<T, true, false> : (const void *)k_acm_persistent<T, false, false>;
     return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(block), args, 0, st);
+}
+
+namespace {
+template <typename T, bool CP>
+cudaError_t launch_cluster_T(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int csize, cudaStream_t st,
+                             int *max_clusters) {
+    auto kern = k_acm_persistent<T, CP, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (max_clusters) return cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg);
+    return cudaLaunchKernelEx(&cfg, kern, cells_dev, ctl);
+}
+}  // namespace
+
+template <typename T>
+cudaError_t acm_launch_persistent_cluster(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int csize, bool cp,
+                                          cudaStream_t st) {
+    if (csize != 8 && csize != 16) return cudaErrorInvalidValue;
+    return cp ? launch_cluster_T<T, true>(cells_dev, ctl, csize, st, nullptr)
+              : launch_cluster_T<T, false>(cells_dev, ctl, csize, st, nullptr);
+}
+
+template <typename T>
+cudaError_t acm_persistent_cluster_ok(int csize, bool cp, bool *ok) {
+    *ok = false;
+    if (csize != 8 && csize != 16) return cudaErrorInvalidValue;
+    int n = 0;
+    cudaError_t e = cp ? launch_cluster_T<T, true>(nullptr, PersistCtl{}, csize, nullptr, &n)
+                       : launch_cluster_T<T, false>(nullptr, PersistCtl{}, csize, nullptr, &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // an unsupported size is an answer, not an error
+        return cudaSuccess;
+    }
+    *ok = n >= 1;
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -326,8 +395,8 @@ cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, true>, block, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, false>, block, 0);
+        e = cp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, true, false>, block, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, false, false>, block, 0);
     *blocks = sms * per;
     return e;
 }
@@ -336,5 +405,9 @@ template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const
 template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, int, bool, cudaStream_t);
 template cudaError_t acm_persistent_max_blocks<float>(int *, int, bool);
 template cudaError_t acm_persistent_max_blocks<double>(int *, int, bool);
+template cudaError_t acm_launch_persistent_cluster<float>(const CellDesc<float> *, const PersistCtl &, int, bool, cudaStream_t);
+template cudaError_t acm_launch_persistent_cluster<double>(const CellDesc<double> *, const PersistCtl &, int, bool, cudaStream_t);
+template cudaError_t acm_persistent_cluster_ok<float>(int, bool, bool *);
+template cudaError_t acm_persistent_cluster_ok<double>(int, bool, bool *);
 
 }  // namespace rbf

@@ -53,5 +53,13 @@ cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl
                                   bool cp, cudaStream_t st);
 template <typename T>
 cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp);
+// the same kernel as one thread-block cluster of csize (8 or 16) CTAs of 256
+// threads, synchronised by the cluster barrier
+template <typename T>
+cudaError_t acm_launch_persistent_cluster(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int csize, bool cp,
+                                          cudaStream_t st);
+// whether a cluster of csize CTAs of the kernel can be scheduled on this device
+template <typename T>
+cudaError_t acm_persistent_cluster_ok(int csize, bool cp, bool *ok);
 
 }  // namespace rbf

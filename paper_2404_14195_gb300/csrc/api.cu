@@ -798,7 +798,15 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
         int rc = save_state(cs[c], sc[c]);
         if (rc) { err = cs[c]->err; return rc; }
     }
-    const int cands[4] = {256, 128, 64, 32};
+    // grid schedules (threads per block) and, where the device can place them, single
+    // clusters of 16 and 8 CTAs (codes -16, -8)
+    std::vector<int> cands = {256, 128, 64, 32};
+    for (int c : {16, 8}) {
+        bool ok = false;
+        if (is_f32(ctx)) CK(acm_persistent_cluster_ok<float>(c, ctx->prec == RBF_FP32C, &ok));
+        else CK(acm_persistent_cluster_ok<double>(c, false, &ok));
+        if (ok) cands.push_back(-c);
+    }
     rbf_tune_report r;
     std::memset(&r, 0, sizeof(r));
     double best = 1e300;
@@ -809,8 +817,11 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
     std::vector<int64_t> st;
     std::vector<double> rs;
     std::vector<int32_t> dn;
-    for (int k = 0; k < 4; ++k) {
-        for (rbf_ctx *x : cs) x->persist_block = cands[k];
+    for (int k = 0; k < (int)cands.size(); ++k) {
+        for (rbf_ctx *x : cs) {
+            x->persist_cluster = cands[k] < 0 ? -cands[k] : 0;
+            if (cands[k] > 0) x->persist_block = cands[k];
+        }
         double ms = 0.0;
         for (int pass = 0; pass < 2; ++pass) {  // warm-up, then the timed trial
             o.max_steps = pass ? trial_steps : 2;
@@ -829,7 +840,10 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
         r.n_candidates = k + 1;
         if (r.ms_per_step[k] < best) { best = r.ms_per_step[k]; best_code = cands[k]; }
     }
-    for (rbf_ctx *x : cs) x->persist_block = best_code;
+    for (rbf_ctx *x : cs) {
+        x->persist_cluster = best_code < 0 ? -best_code : 0;
+        if (best_code > 0) x->persist_block = best_code;
+    }
     r.chosen = best_code;
     r.solver = RBF_SOLVER_ACM;
     if (rep) *rep = r;
@@ -841,9 +855,14 @@ extern "C" {
 
 int rbf_set_persistent_block(rbf_ctx *ctx, int block) {
     if (!ctx) return RBF_EINVAL;
+    if (block == -8 || block == -16) {
+        ctx->persist_cluster = -block;
+        return RBF_OK;
+    }
     if (block != 32 && block != 64 && block != 128 && block != 256)
-        return fail(ctx, RBF_EINVAL, "rbf_set_persistent_block: block must be 32, 64, 128 or 256");
+        return fail(ctx, RBF_EINVAL, "rbf_set_persistent_block: block must be 32, 64, 128, 256, -8 or -16");
     ctx->persist_block = block;
+    ctx->persist_cluster = 0;
     return RBF_OK;
 }
 
@@ -1124,10 +1143,14 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
         for (int64_t s = 0; s < (x->nb + 31) / 32; ++s) wsl.push_back(make_int2(c, (int)s));
     }
     const bool cp = cs[0]->prec == RBF_FP32C;
-    const int block = cs[0]->persist_block, wpb = block / 32;
-    int maxb = 0;
-    CK(acm_persistent_max_blocks<T>(&maxb, block, cp));
-    const int nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + wpb - 1) / wpb)));
+    const int csize = cs[0]->persist_cluster;
+    const int block = csize ? 256 : cs[0]->persist_block, wpb = block / 32;
+    int nblocks = csize;
+    if (!csize) {
+        int maxb = 0;
+        CK(acm_persistent_max_blocks<T>(&maxb, block, cp));
+        nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + wpb - 1) / wpb)));
+    }
     DevArr<CellDesc<T>> d_desc;
     DevArr<int2> d_sl, d_wsl;
     DevArr<unsigned> d_bar;
@@ -1148,7 +1171,8 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
     ctl.nwslices = (int64_t)wsl.size(); ctl.slices = d_sl.p; ctl.wslices = d_wsl.p; ctl.max_steps = o->max_steps;
     ctl.check_every = o->check_every > 0 ? o->check_every : 100; ctl.tol = o->tol; ctl.n_p = cs[0]->n_p;
     CK(cudaEventRecord(ctx->ev0, st));
-    CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, cp, st));
+    if (csize) CK(acm_launch_persistent_cluster<T>(d_desc.p, ctl, csize, cp, st));
+    else CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, cp, st));
     CK(cudaEventRecord(ctx->ev1, st));
     for (rbf_ctx *x : cs) x->launches += 1;
     CK(cudaStreamSynchronize(st));

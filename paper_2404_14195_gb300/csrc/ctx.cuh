@@ -91,6 +91,7 @@ struct rbf_ctx {
     int lbm_layout = rbf::LBM_LAYOUT_PAIRS;  // layout of f32 / f64 (follows the schedule)
     int acm_block = 256;              // threads per block of the ACM sweeps
     int persist_block = 256;          // threads per block of the persistent ACM driver
+    int persist_cluster = 0;          // > 0: run it as one cluster of that many CTAs (8 or 16)
     double persist_ms = 0.0;          // device time of its last launch
     int gblock = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -110,20 +110,20 @@ def test_persistent_block_sizes_give_the_same_fields(rbf):
     s.build_stencils(25)
     s.compute_weights(solver=rbf.RBF_SOLVER_ACM)
     fields = []
-    for block in (256, 128, 64, 32):
+    for block in (256, 128, 64, 32, -16, -8):
         s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=0.01)
         s.set_persistent_block(block)
         r = s.solve(120, 1e-300, check_every=40)
         assert r["steps"] == 120
         fields.append(s.get_fields())
     for f in fields[1:]:
-        assert np.array_equal(f, fields[0])  # block size changes no field arithmetic
+        assert np.array_equal(f, fields[0])  # the schedule changes no field arithmetic
     for c in range(4):
         assert rel_inf(fields[0][:, c], want[:, c]) <= 1e-9, c
     # the tuner restores the state and keeps one of the candidates
     before = s.get_fields()
     times, chosen = s.autotune_persistent(50)
-    assert set(times) == {256, 128, 64, 32} and chosen in times
+    assert {256, 128, 64, 32} <= set(times) <= {256, 128, 64, 32, -16, -8} and chosen in times
     assert np.array_equal(s.get_fields(), before)
     s.step(10)
     want2, _ = oracle.acm_run(case, orc["idx"], orc["w4"], orc["idxb"], orc["wgb"], want, 10, dt=dt, v_ref=0.01)
