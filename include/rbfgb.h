@@ -214,11 +214,13 @@ int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classe
  * rbf_lbm_get_populations reports them, are unchanged. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
 
+#define RBF_TUNE_MAX 16
 typedef struct {
     int solver;          /* RBF_SOLVER_ACM or RBF_SOLVER_LBM */
     int n_candidates;
-    int code[8];         /* LBM: schedule codes of rbf_set_kernel_variant; ACM: threads per block */
-    double ms_per_step[8];
+    int code[RBF_TUNE_MAX];  /* LBM: schedule codes of rbf_set_kernel_variant; ACM: threads per block
+                                (rbf_autotune) or persistent schedule codes (rbf_autotune_persistent) */
+    double ms_per_step[RBF_TUNE_MAX];
     int chosen;          /* the fastest candidate, now in use */
 } rbf_tune_report;
 
@@ -230,23 +232,29 @@ typedef struct {
  * allocates a temporary copy of the state.  2 <= trial_steps <= 2000. */
 int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
 
-/* Autotuner of the persistent ACM driver (rbf_solve): time 256, 128, 64 and 32
- * threads per block (one 32-node slice per warp; the grid is as many blocks as
- * cover the slices, at most the co-resident count, synchronised by a software
- * grid barrier) and, where the device can place them, one thread-block cluster
- * of 16 or 8 CTAs of 256 threads synchronised by the hardware cluster barrier
- * (codes -16, -8; for small cells), over trial_steps steps each, CUDA events
- * around the launch, and keep the fastest for this context's later rbf_solve
- * calls.  Fields and step parity are saved before and restored after the trials.
- * ACM contexts only; 2 <= trial_steps <= 20000.  rep->code[c] is the code of
- * candidate c. */
+/* Autotuner of the persistent ACM driver (rbf_solve): time the schedules 256,
+ * 128, 64, 32 (threads per block, one node per lane), 2128, 4128, 8128, 4256
+ * (2, 4, 8, 4 lanes per node; codes as at rbf_set_persistent_block; the grid is
+ * as many blocks as cover the work, at most the co-resident count, synchronised
+ * by a software grid barrier) and, where the device can place them, one
+ * thread-block cluster of 16 or 8 CTAs synchronised by the hardware cluster
+ * barrier (codes -16, -8), over trial_steps steps each, CUDA events around the
+ * launch, and keep the fastest for this context's later rbf_solve calls.  Fields
+ * and step parity are saved before and restored after the trials.  ACM contexts
+ * only; 2 <= trial_steps <= 20000.  rep->code[c] is the code of candidate c. */
 int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep);
-/* Schedule of the persistent ACM driver for this context: 32, 64, 128 or 256
- * threads per block of a cooperative grid (default 256), or -8 / -16 for one
- * cluster of 8 / 16 CTAs of 256 threads.  A batch launches with its first cell's
- * setting.  The schedule changes only the order of the FP64 residual partial
- * sums, never the fields. */
-int rbf_set_persistent_block(rbf_ctx *ctx, int block);
+/* Schedule of the persistent ACM driver for this context, as a code:
+ *   block + 1000 G   a cooperative grid of `block` (32, 64, 128, 256; default 256)
+ *                    threads per block whose sweeps give each node G lanes (2, 4
+ *                    or 8; write 0 for G = 1, i.e. the code is the block size):
+ *                    the lanes split the node's stencil columns and combine their
+ *                    partial sums with shuffles, multiplying the warps at work on
+ *                    small cells;
+ *   -8, -16          one cluster of 8 / 16 CTAs of 256 threads, G = 1.
+ * A batch launches with its first cell's setting.  With G = 1 the schedule
+ * changes only the order of the FP64 residual partial sums; G > 1 also changes
+ * the order of the stencil sums (rounding only). */
+int rbf_set_persistent_block(rbf_ctx *ctx, int code);
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);

@@ -51,8 +51,8 @@ class rbf_params(ctypes.Structure):
 
 
 class rbf_tune_report(ctypes.Structure):
-    _fields_ = [("solver", ctypes.c_int), ("n_candidates", ctypes.c_int), ("code", ctypes.c_int * 8),
-                ("ms_per_step", ctypes.c_double * 8), ("chosen", ctypes.c_int)]
+    _fields_ = [("solver", ctypes.c_int), ("n_candidates", ctypes.c_int), ("code", ctypes.c_int * 16),
+                ("ms_per_step", ctypes.c_double * 16), ("chosen", ctypes.c_int)]
 
 
 class rbf_batch_cell_result(ctypes.Structure):
@@ -321,10 +321,11 @@ class Solver:
         self._ck(self._L.rbf_autotune(self._h, int(trial_steps), ctypes.byref(r)))
         return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
 
-    def set_persistent_block(self, block: int):
-        """Persistent ACM driver schedule: threads per block of a cooperative grid
-        (32, 64, 128, 256) or -8 / -16 for one cluster of 8 / 16 CTAs."""
-        self._ck(self._L.rbf_set_persistent_block(self._h, int(block)))
+    def set_persistent_block(self, code: int):
+        """Persistent ACM driver schedule code: threads per block (32, 64, 128,
+        256) + 1000 x lanes per node (2, 4, 8; 0 for one), or -8 / -16 for one
+        cluster of 8 / 16 CTAs."""
+        self._ck(self._L.rbf_set_persistent_block(self._h, int(code)))
 
     def autotune_persistent(self, trial_steps: int = 200):
         """ACM: time the persistent driver's block sizes on this case and keep the

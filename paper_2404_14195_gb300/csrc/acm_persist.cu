@@ -66,33 +66,61 @@ __device__ __forceinline__ double slot_C(const unsigned long long *slot, double 
     return beta * (vmax > vref ? vmax : vref);
 }
 
-template <typename T, bool CP>
-__device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool snapshot) {
-    const int64_t i = (ls << 5) + lane;
-    if (i >= c.n) return;
-    const T ui = c.u[i], vi = c.v[i], wi = c.w_[i];
+// Sum over the G consecutive lanes that share a node (G = 1: the value itself).
+template <typename T, int G>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// The phases work on units of 32 / G nodes of one slice: unit `sub` of slice ls
+// holds nodes sub (32 / G) .. (sub + 1) (32 / G) - 1, node nl of the unit on lanes
+// G (nl mod 32/G) .. + G - 1, each lane taking the stencil columns j = g, g + G, ...
+// (g = lane mod G); the group's partial sums are combined with shuffles and the
+// first lane of the group (the lead) writes.  G = 1 is one node per lane.  Every
+// lane reaches the shuffles (no early return before them).
+template <typename T, bool CP, int G>
+__device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int sub, int lane, bool snapshot) {
+    const int nl = sub * (32 / G) + lane / G, g = lane % G;
+    const int64_t i = (ls << 5) + nl;
+    const bool valid = i < c.n;
+    const bool fluid = valid && !c.type[i];
+    T ui = 0, vi = 0, wi = 0;
+    if (valid) { ui = c.u[i]; vi = c.v[i]; wi = c.w_[i]; }
+    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+    if (fluid) {
+        const int n_l = c.n_l;
+        const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + nl;
+        const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + nl;
+#pragma unroll 5
+        for (int j = g; j < n_l; j += G) {
+            const int q = __ldcs(ip + (j << 5));
+            const T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5));
+            const T wz = __ldcs(wp + ((2 * n_l + j) << 5)), wl = __ldcs(wp + ((3 * n_l + j) << 5));
+            const T uq = c.u[q], vq = c.v[q], wq = c.w_[q];
+            gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
+            gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
+            gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            gu[k] = group_sum<T, G>(gu[k]);
+            gv[k] = group_sum<T, G>(gv[k]);
+            gw[k] = group_sum<T, G>(gw[k]);
+        }
+    }
+    if (!valid || g != 0) return;
     if (snapshot) {
         c.uo[i] = ui; c.vo[i] = vi; c.wo[i] = wi;
         if constexpr (CP) { c.uol[i] = c.ul[i]; c.vol[i] = c.vl[i]; c.wol[i] = c.wl[i]; }
     }
-    if (c.type[i]) {
+    if (!fluid) {
         c.us[i] = (T)0; c.vs[i] = (T)0; c.ws[i] = (T)0;
         if constexpr (CP) { c.usl[i] = (T)0; c.vsl[i] = (T)0; c.wsl[i] = (T)0; }
         return;
-    }
-    const int n_l = c.n_l;
-    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
-    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
-    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
-#pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
-        const int q = __ldcs(ip + (j << 5));
-        const T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5));
-        const T wz = __ldcs(wp + ((2 * n_l + j) << 5)), wl = __ldcs(wp + ((3 * n_l + j) << 5));
-        const T uq = c.u[q], vq = c.v[q], wq = c.w_[q];
-        gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
-        gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
-        gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
     }
     const T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
     const T adv_v = ui * gv[0] + vi * gv[1] + wi * gv[2];
@@ -114,24 +142,29 @@ __device__ void phase_predict(const CellDesc<T> &c, int64_t ls, int lane, bool s
     }
 }
 
-template <typename T, bool CP>
-__device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool first, int g) {
-    const int64_t i = (ls << 5) + lane;
-    if (i >= c.n || c.type[i]) return;
+template <typename T, bool CP, int G>
+__device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int sub, int lane, bool first, int gslot) {
+    const int nl = sub * (32 / G) + lane / G, g = lane % G;
+    const int64_t i = (ls << 5) + nl;
+    const bool fluid = i < c.n && !c.type[i];
     const T *u = first ? c.us : c.u;
     const T *v = first ? c.vs : c.v;
     const T *w = first ? c.ws : c.w_;
-    const double C = slot_C(c.vmax + (g ^ 1), c.beta, c.vref);
-    const int n_l = c.n_l;
-    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
-    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
     T div = 0;
+    if (fluid) {
+        const int n_l = c.n_l;
+        const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + nl;
+        const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + nl;
 #pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
-        const int q = __ldcs(ip + (j << 5));
-        div += __ldcs(wp + (j << 5)) * u[q] + __ldcs(wp + ((n_l + j) << 5)) * v[q] +
-               __ldcs(wp + ((2 * n_l + j) << 5)) * w[q];
+        for (int j = g; j < n_l; j += G) {
+            const int q = __ldcs(ip + (j << 5));
+            div += __ldcs(wp + (j << 5)) * u[q] + __ldcs(wp + ((n_l + j) << 5)) * v[q] +
+                   __ldcs(wp + ((2 * n_l + j) << 5)) * w[q];
+        }
     }
+    if constexpr (G > 1) div = group_sum<T, G>(div);
+    if (!fluid || g != 0) return;
+    const double C = slot_C(c.vmax + (gslot ^ 1), c.beta, c.vref);
     const T Ct = (T)C;
     if constexpr (CP) {
         T h = c.p[i], l = c.pl[i];
@@ -142,40 +175,56 @@ __device__ void phase_pressure(const CellDesc<T> &c, int64_t ls, int lane, bool 
     }
 }
 
-template <typename T, bool CP>
-__device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int lane) {
-    const int64_t b = (ls << 5) + lane;
-    if (b >= c.nb) return;
+template <typename T, bool CP, int G>
+__device__ void phase_wall(const CellDesc<T> &c, int64_t ls, int sub, int lane) {
+    const int nl = sub * (32 / G) + lane / G, g = lane % G;
+    const int64_t b = (ls << 5) + nl;
+    const bool valid = b < c.nb;
     const int n_l = c.n_l;
-    const int32_t *__restrict__ ip = c.idxb + ((ls * n_l) << 5) + lane;
-    const T *__restrict__ wp = c.wn + ((ls * n_l) << 5) + lane;
     T acc = 0;
+    if (valid) {
+        const int32_t *__restrict__ ip = c.idxb + ((ls * n_l) << 5) + nl;
+        const T *__restrict__ wp = c.wn + ((ls * n_l) << 5) + nl;
 #pragma unroll 4
-    for (int j = 1; j < n_l; ++j) acc += __ldcs(wp + (j << 5)) * c.p[__ldcs(ip + (j << 5))];
+        for (int j = 1 + g; j < n_l; j += G) acc += __ldcs(wp + (j << 5)) * c.p[__ldcs(ip + (j << 5))];
+    }
+    if constexpr (G > 1) acc = group_sum<T, G>(acc);
+    if (!valid || g != 0) return;
     const int32_t wb = c.wall[b];
-    c.p[wb] = -acc / __ldcs(wp);
+    c.p[wb] = -acc / __ldcs(c.wn + ((ls * n_l) << 5) + nl);
     if constexpr (CP) c.pl[wb] = (T)0;
 }
 
-template <typename T, bool CP>
-__device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int lane) {
-    const int64_t i = (ls << 5) + lane;
-    if (i >= c.n) return 0.0;
-    if (c.type[i]) {
+// returns |v| of the node (lead lane of a fluid node), 0 otherwise
+template <typename T, bool CP, int G>
+__device__ double phase_correct(const CellDesc<T> &c, int64_t ls, int sub, int lane) {
+    const int nl = sub * (32 / G) + lane / G, g = lane % G;
+    const int64_t i = (ls << 5) + nl;
+    const bool valid = i < c.n;
+    const bool fluid = valid && !c.type[i];
+    T gx = 0, gy = 0, gz = 0;
+    if (fluid) {
+        const int n_l = c.n_l;
+        const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + nl;
+        const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + nl;
+#pragma unroll 5
+        for (int j = g; j < n_l; j += G) {
+            const T pq = c.p[__ldcs(ip + (j << 5))];
+            gx += __ldcs(wp + (j << 5)) * pq;
+            gy += __ldcs(wp + ((n_l + j) << 5)) * pq;
+            gz += __ldcs(wp + ((2 * n_l + j) << 5)) * pq;
+        }
+    }
+    if constexpr (G > 1) {
+        gx = group_sum<T, G>(gx);
+        gy = group_sum<T, G>(gy);
+        gz = group_sum<T, G>(gz);
+    }
+    if (!valid || g != 0) return 0.0;
+    if (!fluid) {
         c.u[i] = (T)0; c.v[i] = (T)0; c.w_[i] = (T)0;
         if constexpr (CP) { c.ul[i] = (T)0; c.vl[i] = (T)0; c.wl[i] = (T)0; }
         return 0.0;
-    }
-    const int n_l = c.n_l;
-    const int32_t *__restrict__ ip = c.idx + ((ls * n_l) << 5) + lane;
-    const T *__restrict__ wp = c.w + ((ls * 4 * (int64_t)n_l) << 5) + lane;
-    T gx = 0, gy = 0, gz = 0;
-#pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
-        const T pq = c.p[__ldcs(ip + (j << 5))];
-        gx += __ldcs(wp + (j << 5)) * pq;
-        gy += __ldcs(wp + ((n_l + j) << 5)) * pq;
-        gz += __ldcs(wp + ((2 * n_l + j) << 5)) * pq;
     }
     const T f = c.dt / c.rho;
     T un, vn, wn;
@@ -205,7 +254,7 @@ __device__ __forceinline__ void cluster_barrier() {
 // software barrier's latency dominates a step.  Every block of a cluster takes the
 // same branches at every barrier (the done flags change only before a barrier and
 // the cluster barrier cannot time out), so none is left waiting.
-template <typename T, bool CP, bool CL>
+template <typename T, bool CP, bool CL, int G>
 __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__restrict__ cells, PersistCtl ctl) {
     __shared__ double racc[PERSIST_MAX_CELLS][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,10 +276,10 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
         for (int c = 0; c < ctl.ncells; ++c) any |= !((volatile int32_t *)ctl.done)[c];
         if (!any || (!CL && *(volatile int32_t *)ctl.err)) break;
         const bool check = ((step + 1) % ctl.check_every == 0) || (step + 1 == ctl.max_steps);
-        for (int64_t s = w0; s < ctl.nslices; s += wstride) {
-            const int2 sl = ctl.slices[s];
+        for (int64_t s = w0; s < ctl.nslices * G; s += wstride) {
+            const int2 sl = ctl.slices[s / G];
             if (ctl.done[sl.x]) continue;
-            phase_predict<T, CP>(cells[sl.x], sl.y, lane, check);
+            phase_predict<T, CP, G>(cells[sl.x], sl.y, (int)(s % G), lane, check);
         }
         if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) break;
         bool broke = false;
@@ -243,24 +292,25 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
                     const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
                     c.vmax[g] = 0ULL;
                 }
-            for (int64_t s = w0; s < ctl.nslices; s += wstride) {
-                const int2 sl = ctl.slices[s];
+            for (int64_t s = w0; s < ctl.nslices * G; s += wstride) {
+                const int2 sl = ctl.slices[s / G];
                 if (ctl.done[sl.x]) continue;
                 const CellDesc<T> &c = cells[sl.x];
-                phase_pressure<T, CP>(c, sl.y, lane, it == 0, (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1));
+                phase_pressure<T, CP, G>(c, sl.y, (int)(s % G), lane, it == 0,
+                                         (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1));
             }
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
-            for (int64_t s = w0; s < ctl.nwslices; s += wstride) {
-                const int2 sl = ctl.wslices[s];
+            for (int64_t s = w0; s < ctl.nwslices * G; s += wstride) {
+                const int2 sl = ctl.wslices[s / G];
                 if (ctl.done[sl.x]) continue;
-                phase_wall<T, CP>(cells[sl.x], sl.y, lane);
+                phase_wall<T, CP, G>(cells[sl.x], sl.y, (int)(s % G), lane);
             }
             if (!grid_barrier(ctl.bar_count, ctl.bar_gen, nblocks, ctl.err)) { broke = true; break; }
-            for (int64_t s = w0; s < ctl.nslices; s += wstride) {
-                const int2 sl = ctl.slices[s];
+            for (int64_t s = w0; s < ctl.nslices * G; s += wstride) {
+                const int2 sl = ctl.slices[s / G];
                 if (ctl.done[sl.x]) continue;
                 const CellDesc<T> &c = cells[sl.x];
-                double sp = phase_correct<T, CP>(c, sl.y, lane);
+                double sp = phase_correct<T, CP, G>(c, sl.y, (int)(s % G), lane);
                 for (int off = 16; off > 0; off >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, off));
                 if (lane == 0 && sp > 0.0) {
                     const int g = (int)((c.parity0 + (int64_t)ctl.n_p * step + it) & 1);
@@ -332,12 +382,25 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
 
 bool persist_block_ok(int block) { return block == 32 || block == 64 || block == 128 || block == 256; }
 
+namespace {
+template <typename T, bool CP>
+const void *grid_kernel(int group) {
+    switch (group) {
+    case 1: return (const void *)k_acm_persistent<T, CP, false, 1>;
+    case 2: return (const void *)k_acm_persistent<T, CP, false, 2>;
+    case 4: return (const void *)k_acm_persistent<T, CP, false, 4>;
+    case 8: return (const void *)k_acm_persistent<T, CP, false, 8>;
+    default: return nullptr;
+    }
+}
+}  // namespace
+
 template <typename T>
 cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, int block,
-                                  bool cp, cudaStream_t st) {
-    if (!persist_block_ok(block) || nblocks < 1) return cudaErrorInvalidValue;
+                                  int group, bool cp, cudaStream_t st) {
+    const void *fn = cp ? grid_kernel<T, true>(group) : grid_kernel<T, false>(group);
+    if (!persist_block_ok(block) || nblocks < 1 || !fn) return cudaErrorInvalidValue;
     void *args[] = {(void *)&cells_dev, (void *)&ctl};
-    const void *fn = cp ? (const void *)k_acm_persistent<T, true, false> : (const void *)k_acm_persistent<T, false, false>;
     return cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(block), args, 0, st);
 }
 
@@ -345,7 +408,7 @@ namespace {
 template <typename T, bool CP>
 cudaError_t launch_cluster_T(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int csize, cudaStream_t st,
                              int *max_clusters) {
-    auto kern = k_acm_persistent<T, CP, true>;
+    auto kern = k_acm_persistent<T, CP, true, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
@@ -389,22 +452,21 @@ cudaError_t acm_persistent_cluster_ok(int csize, bool cp, bool *ok) {
 }
 
 template <typename T>
-cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp) {
-    if (!persist_block_ok(block)) return cudaErrorInvalidValue;
+cudaError_t acm_persistent_max_blocks(int *blocks, int block, int group, bool cp) {
+    const void *fn = cp ? grid_kernel<T, true>(group) : grid_kernel<T, false>(group);
+    if (!persist_block_ok(block) || !fn) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, true, false>, block, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_acm_persistent<T, false, false>, block, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, 0);
     *blocks = sms * per;
     return e;
 }
 
-template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const PersistCtl &, int, int, bool, cudaStream_t);
-template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, int, bool, cudaStream_t);
-template cudaError_t acm_persistent_max_blocks<float>(int *, int, bool);
-template cudaError_t acm_persistent_max_blocks<double>(int *, int, bool);
+template cudaError_t acm_launch_persistent<float>(const CellDesc<float> *, const PersistCtl &, int, int, int, bool, cudaStream_t);
+template cudaError_t acm_launch_persistent<double>(const CellDesc<double> *, const PersistCtl &, int, int, int, bool, cudaStream_t);
+template cudaError_t acm_persistent_max_blocks<float>(int *, int, int, bool);
+template cudaError_t acm_persistent_max_blocks<double>(int *, int, int, bool);
 template cudaError_t acm_launch_persistent_cluster<float>(const CellDesc<float> *, const PersistCtl &, int, bool, cudaStream_t);
 template cudaError_t acm_launch_persistent_cluster<double>(const CellDesc<double> *, const PersistCtl &, int, bool, cudaStream_t);
 template cudaError_t acm_persistent_cluster_ok<float>(int, bool, bool *);

@@ -47,12 +47,13 @@ struct PersistCtl {
 };
 
 // cp selects the compensated kernel (every cell then carries low words); block:
-// threads per block, 32, 64, 128 or 256 (one 32-node slice per warp at a time)
+// threads per block, 32, 64, 128 or 256; group: lanes per node, 1, 2, 4 or 8 (a
+// warp takes 32 / group nodes of a slice at a time)
 template <typename T>
 cudaError_t acm_launch_persistent(const CellDesc<T> *cells_dev, const PersistCtl &ctl, int nblocks, int block,
-                                  bool cp, cudaStream_t st);
+                                  int group, bool cp, cudaStream_t st);
 template <typename T>
-cudaError_t acm_persistent_max_blocks(int *blocks, int block, bool cp);
+cudaError_t acm_persistent_max_blocks(int *blocks, int block, int group, bool cp);
 // the same kernel as one thread-block cluster of csize (8 or 16) CTAs of 256
 // threads, synchronised by the cluster barrier
 template <typename T>

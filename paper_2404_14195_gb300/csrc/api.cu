@@ -744,7 +744,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     std::memset(&r, 0, sizeof(r));
     double best = 1e300;
     int best_code = cands[0];
-    for (size_t c = 0; c < cands.size() && c < 8; ++c) {
+    for (size_t c = 0; c < cands.size() && c < RBF_TUNE_MAX; ++c) {
         if (ctx->solver == RBF_SOLVER_LBM) {
             rc = switch_schedule(ctx, cands[c]);
             if (rc) return rc;
@@ -786,6 +786,25 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
 }  // extern "C"
 
 namespace {
+// schedule code of the persistent driver: block (32 .. 256) + 1000 group for a grid
+// with `group` lanes per node (group 1: the code is the block size), -8 / -16 for a
+// cluster; false for anything else
+bool persist_code_ok(int code) {
+    if (code == -8 || code == -16) return true;
+    const int block = code % 1000, group = code / 1000;
+    return (block == 32 || block == 64 || block == 128 || block == 256) &&
+           (group == 0 || group == 2 || group == 4 || group == 8);
+}
+void set_persist_code(rbf_ctx *x, int code) {
+    if (code < 0) {
+        x->persist_cluster = -code;
+        return;
+    }
+    x->persist_cluster = 0;
+    x->persist_block = code % 1000;
+    x->persist_group = code / 1000 ? code / 1000 : 1;
+}
+
 // Time the persistent driver over `cs` for every block size and keep the fastest
 // in every cell; the cells' fields and parities are restored after each trial.
 int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report *rep, std::string &err) {
@@ -798,9 +817,10 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
         int rc = save_state(cs[c], sc[c]);
         if (rc) { err = cs[c]->err; return rc; }
     }
-    // grid schedules (threads per block) and, where the device can place them, single
-    // clusters of 16 and 8 CTAs (codes -16, -8)
-    std::vector<int> cands = {256, 128, 64, 32};
+    // grid schedules (code = threads per block + 1000 (lanes per node - 1 ... ) as
+    // described at rbf_set_persistent_block) and, where the device can place them,
+    // single clusters of 16 and 8 CTAs (codes -16, -8)
+    std::vector<int> cands = {256, 128, 64, 32, 2128, 4128, 8128, 4256};
     for (int c : {16, 8}) {
         bool ok = false;
         if (is_f32(ctx)) CK(acm_persistent_cluster_ok<float>(c, ctx->prec == RBF_FP32C, &ok));
@@ -817,11 +837,8 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
     std::vector<int64_t> st;
     std::vector<double> rs;
     std::vector<int32_t> dn;
-    for (int k = 0; k < (int)cands.size(); ++k) {
-        for (rbf_ctx *x : cs) {
-            x->persist_cluster = cands[k] < 0 ? -cands[k] : 0;
-            if (cands[k] > 0) x->persist_block = cands[k];
-        }
+    for (int k = 0; k < (int)cands.size() && k < RBF_TUNE_MAX; ++k) {
+        for (rbf_ctx *x : cs) set_persist_code(x, cands[k]);
         double ms = 0.0;
         for (int pass = 0; pass < 2; ++pass) {  // warm-up, then the timed trial
             o.max_steps = pass ? trial_steps : 2;
@@ -840,10 +857,7 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
         r.n_candidates = k + 1;
         if (r.ms_per_step[k] < best) { best = r.ms_per_step[k]; best_code = cands[k]; }
     }
-    for (rbf_ctx *x : cs) {
-        x->persist_cluster = best_code < 0 ? -best_code : 0;
-        if (best_code > 0) x->persist_block = best_code;
-    }
+    for (rbf_ctx *x : cs) set_persist_code(x, best_code);
     r.chosen = best_code;
     r.solver = RBF_SOLVER_ACM;
     if (rep) *rep = r;
@@ -853,16 +867,12 @@ int tune_persistent(std::vector<rbf_ctx *> &cs, int trial_steps, rbf_tune_report
 
 extern "C" {
 
-int rbf_set_persistent_block(rbf_ctx *ctx, int block) {
+int rbf_set_persistent_block(rbf_ctx *ctx, int code) {
     if (!ctx) return RBF_EINVAL;
-    if (block == -8 || block == -16) {
-        ctx->persist_cluster = -block;
-        return RBF_OK;
-    }
-    if (block != 32 && block != 64 && block != 128 && block != 256)
-        return fail(ctx, RBF_EINVAL, "rbf_set_persistent_block: block must be 32, 64, 128, 256, -8 or -16");
-    ctx->persist_block = block;
-    ctx->persist_cluster = 0;
+    if (!persist_code_ok(code))
+        return fail(ctx, RBF_EINVAL, "rbf_set_persistent_block: code = block (32, 64, 128, 256) + 1000 x lanes per "
+                                     "node (2, 4, 8; 0 for 1), or -8 / -16");
+    set_persist_code(ctx, code);
     return RBF_OK;
 }
 
@@ -1145,11 +1155,13 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
     const bool cp = cs[0]->prec == RBF_FP32C;
     const int csize = cs[0]->persist_cluster;
     const int block = csize ? 256 : cs[0]->persist_block, wpb = block / 32;
+    const int group = csize ? 1 : cs[0]->persist_group;
     int nblocks = csize;
     if (!csize) {
         int maxb = 0;
-        CK(acm_persistent_max_blocks<T>(&maxb, block, cp));
-        nblocks = std::max(1, std::min<int>(maxb, (int)((sl.size() + wpb - 1) / wpb)));
+        CK(acm_persistent_max_blocks<T>(&maxb, block, group, cp));
+        const int64_t units = (int64_t)sl.size() * group;  // work units of 32 / group nodes
+        nblocks = std::max(1, std::min<int>(maxb, (int)((units + wpb - 1) / wpb)));
     }
     DevArr<CellDesc<T>> d_desc;
     DevArr<int2> d_sl, d_wsl;
@@ -1172,7 +1184,7 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
     ctl.check_every = o->check_every > 0 ? o->check_every : 100; ctl.tol = o->tol; ctl.n_p = cs[0]->n_p;
     CK(cudaEventRecord(ctx->ev0, st));
     if (csize) CK(acm_launch_persistent_cluster<T>(d_desc.p, ctl, csize, cp, st));
-    else CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, cp, st));
+    else CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, group, cp, st));
     CK(cudaEventRecord(ctx->ev1, st));
     for (rbf_ctx *x : cs) x->launches += 1;
     CK(cudaStreamSynchronize(st));

@@ -92,6 +92,7 @@ struct rbf_ctx {
     int acm_block = 256;              // threads per block of the ACM sweeps
     int persist_block = 256;          // threads per block of the persistent ACM driver
     int persist_cluster = 0;          // > 0: run it as one cluster of that many CTAs (8 or 16)
+    int persist_group = 1;            // lanes per node of its sweeps (1, 2, 4, 8)
     double persist_ms = 0.0;          // device time of its last launch
     int gblock = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

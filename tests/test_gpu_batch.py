@@ -120,10 +120,20 @@ def test_persistent_block_sizes_give_the_same_fields(rbf):
         assert np.array_equal(f, fields[0])  # the schedule changes no field arithmetic
     for c in range(4):
         assert rel_inf(fields[0][:, c], want[:, c]) <= 1e-9, c
+    # several lanes per node: the stencil sums are split and recombined (rounding only)
+    for code in (2128, 4128, 8128, 4256, 8032):
+        s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=0.01)
+        s.set_persistent_block(code)
+        r = s.solve(120, 1e-300, check_every=40)
+        assert r["steps"] == 120
+        got = s.get_fields()
+        for c in range(4):
+            assert rel_inf(got[:, c], want[:, c]) <= 1e-9, (code, c)
     # the tuner restores the state and keeps one of the candidates
     before = s.get_fields()
     times, chosen = s.autotune_persistent(50)
-    assert {256, 128, 64, 32} <= set(times) <= {256, 128, 64, 32, -16, -8} and chosen in times
+    assert {256, 128, 64, 32, 2128, 4128, 8128, 4256} <= set(times) <= {256, 128, 64, 32, 2128, 4128, 8128, 4256,
+                                                                           -16, -8} and chosen in times
     assert np.array_equal(s.get_fields(), before)
     s.step(10)
     want2, _ = oracle.acm_run(case, orc["idx"], orc["w4"], orc["idxb"], orc["wgb"], want, 10, dt=dt, v_ref=0.01)

@@ -51,7 +51,10 @@ def test_fp32c_fixed_steps_multilaunch_and_persistent(rbf, cell, orc):
     b = _solver(rbf, cell, rbf.RBF_FP32C, dt=dt, v_ref=0.01)
     r = b.solve(200, 1e-300, check_every=50)
     assert r["steps"] == 200
-    for s in (a, b):
+    c = _solver(rbf, cell, rbf.RBF_FP32C, dt=dt, v_ref=0.01)
+    c.set_persistent_block(4128)  # four lanes per node
+    assert c.solve(200, 1e-300, check_every=50)["steps"] == 200
+    for s in (a, b, c):
         got = s.get_fields()
         for c in range(4):
             assert rel_inf(got[:, c], want[:, c]) <= 1e-4, c
