@@ -417,9 +417,10 @@ class Batch:
         self._ck(self._L.rbf_batch_solve(self._h, ctypes.byref(o), res), ok=(RBF_OK, RBF_ENOTCONVERGED))
         return [dict(steps=r.steps, residual=r.residual, k_over_d2=r.k_over_d2, status=r.status) for r in res]
 
-    def set_persistent_block(self, block: int):
+    def set_persistent_block(self, code: int):
+        """Persistent-driver schedule code for every cell (see Solver.set_persistent_block)."""
         for i in range(len(self._cells)):
-            self.cell(i).set_persistent_block(block)
+            self.cell(i).set_persistent_block(code)
 
     def autotune(self, trial_steps: int = 100):
         """Time the persistent driver's block sizes over all cells and keep the

@@ -50,10 +50,12 @@ def output_scale(targets):
     return np.where(s > 0.0, s, 1.0)
 
 
-def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0, normalise=True):
+def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0, normalise=True, decay=()):
     """Train the network on (xyz, radius, sdf, targets); with `normalise` each
     output is divided by its RMS for training and the network's out_scale set to
-    match, so warm_start writes fields in the solver's units."""
+    match, so warm_start writes fields in the solver's units.  `decay`: further
+    (steps, lr) phases run after the first (Adam's moments carry over; each phase
+    draws its batches with its own seed)."""
     m = Mlp(device)
     m.set_params(np.asarray(init_params, np.float32))
     xyz, rad, sdf, tgt = data
@@ -62,8 +64,10 @@ def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0, 
         tgt = (np.asarray(tgt, np.float64) / m.out_scale).astype(np.float32)
     m.set_data(xyz, rad, sdf, tgt)
     t0 = time.perf_counter()
-    hist = m.train(steps, batch, lr, seed)
-    return m, hist, time.perf_counter() - t0
+    hist = [m.train(steps, batch, lr, seed)]
+    for k, (st, lr_k) in enumerate(decay):
+        hist.append(m.train(st, batch, lr_k, seed + 1 + k))
+    return m, np.concatenate(hist), time.perf_counter() - t0
 
 
 def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32C, tol=1e-6, max_steps=2_000_000,
