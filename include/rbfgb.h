@@ -163,6 +163,21 @@ int rbf_permeability(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q);
  * rbf_permeability(m_p).  FP64 accumulation. */
 int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K);
 
+/* Pointwise velocity difference of two solutions on the same nodes (the
+ * cross-validation of the section "Pointwise comparison of the meshless
+ * solvers", Eq. pointwise_error): per node, in the caller's node order,
+ *   dv[i]    = |v_a(x_i) - v_b(x_i)|_2
+ *   delta[i] = dv[i] / |v_b(x_i)|_2   (NaN where v_b(x_i) = 0, e.g. wall nodes)
+ * with velocities in physical units (LBM: lattice velocity times dx/dt_LBM, the
+ * same conversion as rbf_get_fields; compensated FP32: hi + lo).  The paper's
+ * delta takes a = the MLBM context and b = the MNS context; any two initialised
+ * contexts with the same node count on one device are accepted (the nodes are
+ * not compared: the caller gives both the same rbf_set_case input).
+ * delta, dv: host arrays of n doubles, either may be NULL.  a == b, different
+ * devices or node counts -> RBF_EINVAL.  Runs on a's stream, then b's; both
+ * streams are synchronised on return.  */
+int rbf_pointwise_difference(rbf_ctx *a, rbf_ctx *b, double *delta, double *dv);
+
 /* Relative velocity change |v - v_prev|_2 / |v|_2 over fluid nodes over the last
  * step (ACM), FP64 accumulation; computed when the last rbf_step ran with
  * residual tracking (rbf_solve does).  */
@@ -258,6 +273,12 @@ int rbf_set_persistent_block(rbf_ctx *ctx, int code);
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
+
+/* Physical time step of one rbf_step: ACM delta t = cfl h_min^2 / (2 nu) (the MNS
+ * section) or the rbf_params value; LBM delta t = nu_lb dx^2 / nu (Eq.
+ * conversion_factors).  Needs rbf_init.  For the stopping criterion of
+ * Eq. stopCrit, whose window Delta t is in physical time. */
+int rbf_time_step(rbf_ctx *ctx, double *dt);
 
 /* ---- batched cells ----------------------------------------------------------
  * Many periodic cells (their own nodes, sphere and stencil size N_L), e.g. a

@@ -411,3 +411,25 @@ def drag(case, idx, wgrad_wall, uvwp, nu: float, rho: float = 1.0, area: float =
 def drag_coefficient(fx: float, r: float, q: float, nu: float, rho: float = 1.0) -> float:
     """K = F_{H,0} / (6 pi r phi q mu), Eq. K_definition, mu = rho nu."""
     return fx / (6.0 * np.pi * r * porosity(r) * q * rho * nu)
+
+
+def pointwise_difference(v_a, v_b):
+    """Eq. pointwise_error of the pointwise comparison section: per node,
+    dv = |v_a - v_b| and delta = dv / |v_b|, |.| the Euclidean norm of the
+    velocity vector (the paper takes a = MLBM, b = MNS).  delta is NaN where
+    v_b = 0.  v_a, v_b: (n, 3).  Returns (delta, dv)."""
+    a = np.asarray(v_a, np.float64)
+    b = np.asarray(v_b, np.float64)
+    dv = np.sqrt(((a - b) ** 2).sum(1))
+    nb = np.sqrt((b * b).sum(1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        delta = np.where(nb > 0.0, dv / np.where(nb > 0.0, nb, 1.0), np.nan)
+    return delta, dv
+
+
+def stop_criterion(k_now: float, k_prev: float, window: float) -> float:
+    """|Delta|_{k/d^2} of Eq. stopCrit: the change of k/d^2 over the last window
+    of physical length `window` (the paper's Delta t = 10^4 delta t), relative
+    to the current value and per unit time.  The paper stops once it is below
+    10^-2."""
+    return abs(k_now - k_prev) / (abs(k_now) * window)

@@ -93,6 +93,8 @@ ABI = {
     "rbf_lbm_set_populations": (_I, [_P, _P]),
     "rbf_permeability": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "rbf_drag": (_I, [_P, _I, _P, ctypes.POINTER(_D)]),
+    "rbf_pointwise_difference": (_I, [_P, _P, _P, _P]),
+    "rbf_time_step": (_I, [_P, ctypes.POINTER(_D)]),
     "rbf_solve": (_I, [_P, ctypes.POINTER(rbf_solve_opts), ctypes.POINTER(rbf_solve_result)]),
     "rbf_last_step_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "rbf_launch_count": (_I64, [_P]),
@@ -284,6 +286,11 @@ class Solver:
         self._ck(self._L.rbf_drag(self._h, m_p, _ptr(F), ctypes.byref(K)))
         return F, K.value
 
+    def pointwise_difference(self, other: "Solver"):
+        """(delta, dv) of Eq. pointwise_error with v_a = this context's velocity and
+        v_b = other's, per node in the caller's order (delta NaN where v_b = 0)."""
+        return pointwise_difference(self, other)
+
     def solve(self, max_steps: int, tol: float, check_every: int = 100, m_p: int = 32, raise_on_cap=False):
         o = rbf_solve_opts(max_steps, check_every, tol, m_p)
         r = rbf_solve_result()
@@ -335,8 +342,26 @@ class Solver:
         self._ck(self._L.rbf_autotune_persistent(self._h, int(trial_steps), ctypes.byref(r)))
         return {r.code[i]: r.ms_per_step[i] for i in range(r.n_candidates)}, r.chosen
 
+    def time_step(self) -> float:
+        """Physical time of one step (ACM delta t, or the LBM delta t)."""
+        d = ctypes.c_double()
+        self._ck(self._L.rbf_time_step(self._h, ctypes.byref(d)))
+        return d.value
+
     def launch_count(self) -> int:
         return int(self._L.rbf_launch_count(self._h))
+
+
+def pointwise_difference(a: Solver, b: Solver):
+    """rbf_pointwise_difference: (delta, dv) of Eq. pointwise_error between two
+    initialised contexts on the same nodes (paper: a = MLBM, b = MNS)."""
+    n = a.n
+    delta, dv = np.empty(n), np.empty(n)
+    rc = a._L.rbf_pointwise_difference(a._h, b._h, _ptr(delta), _ptr(dv))
+    if rc != RBF_OK:
+        msg = a._L.rbf_last_error(a._h).decode() or a._L.rbf_last_error(b._h).decode()
+        raise RbfError(rc, msg)
+    return delta, dv
 
 
 def _params(precision=RBF_FP64, nu=1.0, g=(1.0, 0.0, 0.0), rho=1.0, dt=0.0, cfl=0.1, beta=10.0, v_ref=0.0,

@@ -292,6 +292,13 @@ const char *rbf_last_error(const rbf_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t rbf_launch_count(const rbf_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
+int rbf_time_step(rbf_ctx *ctx, double *dt) {
+    if (!ctx || !dt) return RBF_EINVAL;
+    if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_time_step: not initialised");
+    *dt = ctx->dt;
+    return RBF_OK;
+}
+
 int rbf_set_nodes(rbf_ctx *ctx, int64_t n, const double *xyz, const uint8_t *type, const double *normal) {
     if (!ctx) return RBF_EINVAL;
     if (n < 2 || n > (int64_t)INT32_MAX / 64 || !xyz || !type) return fail(ctx, RBF_EINVAL, "rbf_set_nodes: bad n or null array");
@@ -1111,6 +1118,57 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
         if (rc) return rc;
         *K = F[0] / (6.0 * M_PI * ctx->r * porosity_of(ctx->r) * qq * mu);
     }
+    return RBF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// A context's velocity (physical units, FP64) scattered into out[3n] in the
+// caller's node order.
+int velocity_to(rbf_ctx *ctx, double *out) {
+    if (ctx->solver == RBF_SOLVER_ACM) {
+        if (ctx->prec == RBF_FP32C)
+            CK(launch_velocity<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->l32[0].p, ctx->l32[1].p, ctx->l32[2].p, 1, 1.0, out, ctx->st));
+        else if (is_f32(ctx))
+            CK(launch_velocity<float>(ctx->n, ctx->perm.p, ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, nullptr, nullptr, nullptr, 1, 1.0, out, ctx->st));
+        else
+            CK(launch_velocity<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, nullptr, nullptr, nullptr, 1, 1.0, out, ctx->st));
+        ++ctx->launches;
+    } else {
+        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        const double *m = ctx->mac.p;
+        CK(launch_velocity<double>(ctx->n, ctx->perm.p, m, m + 1, m + 2, nullptr, nullptr, nullptr, 4, ctx->dx / ctx->lbm_dt, out, ctx->st));
+        ctx->launches += 2;
+    }
+    return RBF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rbf_pointwise_difference(rbf_ctx *a, rbf_ctx *b, double *delta, double *dv) {
+    if (!a || !b || a == b) return RBF_EINVAL;
+    if (!a->inited || !b->inited) return fail(a, RBF_EINVAL, "rbf_pointwise_difference: not initialised");
+    if (a->device != b->device) return fail(a, RBF_EINVAL, "rbf_pointwise_difference: contexts on different devices");
+    if (a->n != b->n) return fail(a, RBF_EINVAL, "rbf_pointwise_difference: node counts differ");
+    if (!delta && !dv) return RBF_OK;
+    DeviceGuard dg(a->device);
+    const int64_t n = a->n;
+    rbf_ctx *ctx = a;  // for CK's error reporting
+    // stage holds at least 4n doubles: [0, 3n) velocity, [3n, 4n) one output
+    int rc = velocity_to(a, a->stage.p);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(a->st));
+    rc = velocity_to(b, b->stage.p);
+    if (rc) return rc;
+    ctx = b;
+    CK(launch_pointwise(n, a->stage.p, b->stage.p, a->stage.p + 3 * n, b->stage.p + 3 * n, b->st));
+    ++b->launches;
+    if (delta) CK(cudaMemcpyAsync(delta, a->stage.p + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    if (dv) CK(cudaMemcpyAsync(dv, b->stage.p + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
     return RBF_OK;
 }
 

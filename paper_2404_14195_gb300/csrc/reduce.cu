@@ -245,6 +245,51 @@ cudaError_t launch_acm_import_pair(int64_t n, const int32_t *perm, float *u, flo
     return cudaGetLastError();
 }
 
+// Velocity of a context in physical units, scattered to the caller's node order:
+// out[3 perm[i] + c] = scale (v_c[i stride] + lo_c[i]), lo null for a plain state.
+template <typename T>
+__global__ void k_velocity(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *ul,
+                           const T *vl, const T *wl, int64_t stride, double scale, double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = (double)u[i * stride], y = (double)v[i * stride], z = (double)w[i * stride];
+    if (ul) {
+        x += (double)ul[i];
+        y += (double)vl[i];
+        z += (double)wl[i];
+    }
+    const int64_t o = 3 * (int64_t)perm[i];
+    out[o] = scale * x;
+    out[o + 1] = scale * y;
+    out[o + 2] = scale * z;
+}
+template <typename T>
+cudaError_t launch_velocity(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *ul,
+                            const T *vl, const T *wl, int64_t stride, double scale, double *out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_velocity<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, u, v, w, ul, vl, wl, stride, scale, out);
+    return cudaGetLastError();
+}
+
+// Eq. pointwise_error on [n][3] velocity fields in one node order:
+// dv = |v_a - v_b|_2, delta = dv / |v_b|_2 (NaN where v_b = 0)
+__global__ void k_pointwise(int64_t n, const double *va, const double *vb, double *delta, double *dv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double bx = vb[3 * i], by = vb[3 * i + 1], bz = vb[3 * i + 2];
+    const double x = va[3 * i] - bx, y = va[3 * i + 1] - by, z = va[3 * i + 2] - bz;
+    const double d = sqrt(x * x + y * y + z * z);
+    const double nb = sqrt(bx * bx + by * by + bz * bz);
+    dv[i] = d;
+    delta[i] = nb > 0.0 ? d / nb : __longlong_as_double(0x7ff8000000000000LL);
+}
+cudaError_t launch_pointwise(int64_t n, const double *va, const double *vb, double *delta, double *dv,
+                             cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_pointwise<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, va, vb, delta, dv);
+    return cudaGetLastError();
+}
+
 // LBM macro buffer (sorted, lattice units, (vx, vy, vz, drho)) -> physical uvwp, caller order
 __global__ void k_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
                              const double *drho_sum, double *out) {
@@ -322,7 +367,9 @@ cudaError_t launch_export_weights(int64_t n, int n_l, int n_ops, int op, const i
                                               const T *, double *, cudaStream_t);                               \
     template cudaError_t launch_acm_import<T>(int64_t, const int32_t *, T *, T *, T *, T *, const double *,      \
                                               cudaStream_t);                                                    \
-    template cudaError_t launch_nonfinite<T>(const T *, int64_t, int32_t *, cudaStream_t);
+    template cudaError_t launch_nonfinite<T>(const T *, int64_t, int32_t *, cudaStream_t);                    \
+    template cudaError_t launch_velocity<T>(int64_t, const int32_t *, const T *, const T *, const T *, const T *, \
+                                            const T *, const T *, int64_t, double, double *, cudaStream_t);
 RBF_RED_INST(float)
 RBF_RED_INST(double)
 

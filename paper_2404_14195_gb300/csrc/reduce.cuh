@@ -39,6 +39,14 @@ cudaError_t launch_acm_import_pair(int64_t n, const int32_t *perm, float *u, flo
                                    float *ul, float *vl, float *wl, float *pl, const double *in, cudaStream_t st);
 template <typename T>
 cudaError_t launch_nonfinite(const T *a, int64_t n, int32_t *flag, cudaStream_t st);
+// velocity scale (u[i stride] + ul[i], ...) scattered to caller order [n][3] FP64
+// (ul, vl, wl null for a plain state)
+template <typename T>
+cudaError_t launch_velocity(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *ul,
+                            const T *vl, const T *wl, int64_t stride, double scale, double *out, cudaStream_t st);
+// pointwise difference of two [n][3] velocity fields in one node order
+cudaError_t launch_pointwise(int64_t n, const double *va, const double *vb, double *delta, double *dv,
+                             cudaStream_t st);
 cudaError_t launch_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
                               const double *drho_sum, double *out, cudaStream_t st);
 cudaError_t launch_export_stencils(int64_t n, int n_l, const int32_t *perm, const int32_t *iperm,

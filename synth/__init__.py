@@ -69,6 +69,8 @@ def _load():
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, P, P,
                                                ctypes.c_int64]
+            lib.sg_advancing_front_gauss.restype = ctypes.c_int64
+            lib.sg_advancing_front_gauss.argtypes = lib.sg_advancing_front.argtypes
             lib.sg_rng_stream.restype = ctypes.c_uint64
             lib.sg_rng_stream.argtypes = [ctypes.c_uint64, ctypes.c_int64, P]
             _lib = lib
@@ -146,6 +148,32 @@ def refined_cell(r: float = 0.4, h_min: float = 0.008, h_max: float = 0.04, ramp
     nrm[:nb] = wn
     return Case(xyz=out[:m].copy(), type=typ, normal=nrm, centre=c, radius=float(r),
                 h_min=h_min, h_max=h_max, seed=seed, kind="refined")
+
+
+def gaussian_cell(r: float = 0.062, h_min: float = 0.01, h_max: float | None = None, eps: float = 0.295,
+                  seed: int = 2, wall_gap: float = 0.5, excl: float = 0.87, n_cand: int = 24,
+                  centre=(0.5, 0.5, 0.5), cap: int | None = None) -> Case:
+    """h-refined cell with the paper's Gaussian spacing (Eq. refinement_function):
+    h = h_max - exp(-t^2 / (2 eps^2)) (h_max - h_min), t = wall distance / (sqrt(3)/2 - r);
+    defaults h_max = 2 h_min and eps = 0.295 as in the paper's runs."""
+    if h_max is None:
+        h_max = 2.0 * h_min
+    c = np.ascontiguousarray(centre, np.float64)
+    wxyz, wn = sphere_surface(c, r, h_min)
+    if cap is None:
+        cap = int(4.0 / h_min ** 3) + len(wxyz) + 1024
+    out = np.empty((cap, 3), np.float64)
+    m = _load().sg_advancing_front_gauss(_ptr(c), r, h_min, h_max, eps, wall_gap, excl, n_cand, seed,
+                                         len(wxyz), _ptr(np.ascontiguousarray(wxyz)), _ptr(out), cap)
+    if m < 0:
+        raise RuntimeError(f"advancing_front_gauss failed ({m})")
+    nb = len(wxyz)
+    typ = np.zeros(m, np.uint8)
+    typ[:nb] = WALL
+    nrm = np.zeros((m, 3))
+    nrm[:nb] = wn
+    return Case(xyz=out[:m].copy(), type=typ, normal=nrm, centre=c, radius=float(r),
+                h_min=h_min, h_max=h_max, seed=seed, kind="gaussian")
 
 
 def channel(h: float = 0.05, H: float = 0.5, jitter: float = 0.2, seed: int = 3) -> Case:

@@ -122,11 +122,24 @@ static int64_t sg_cell_of(const sg_grid *G, const double x[3]) {
     return ((int64_t)i * G->g + j) * G->g + k;
 }
 
-static double sg_h_of(double d, double h_min, double h_max, double ramp) {
-    double t = d / ramp;
+/* Target spacing at wall distance d.  mode 0: linear ramp h_min + (h_max - h_min)
+ * min(1, d / shape).  mode 1: the Gaussian of Eq. refinement_function,
+ * h_max - exp(-t^2 / (2 shape^2)) (h_max - h_min) with t = d / (sqrt(3)/2 - r) the
+ * wall distance over its largest value in the cell (shape = epsilon). */
+typedef struct {
+    int mode;
+    double h_min, h_max, shape, dmax;
+} sg_spacing;
+
+static double sg_h_of(const sg_spacing *S, double d) {
+    if (S->mode == 1) {
+        double t = d / S->dmax;
+        return S->h_max - exp(-t * t / (2.0 * S->shape * S->shape)) * (S->h_max - S->h_min);
+    }
+    double t = d / S->shape;
     if (t > 1.0) t = 1.0;
     if (t < 0.0) t = 0.0;
-    return h_min + (h_max - h_min) * t;
+    return S->h_min + (S->h_max - S->h_min) * t;
 }
 
 /* Is there a node within distance `rad` of x (periodic)? */
@@ -152,14 +165,14 @@ static int sg_too_close(const sg_grid *G, const double *pts, const double x[3], 
 }
 
 /* Fill the fluid part of the periodic cell.  `seed_xyz` (n_seed nodes, e.g. the wall
- * nodes) are placed first and seed the queue.  Spacing h(d) = h_min + (h_max-h_min)
- * * min(1, d/ramp) with d the wall distance; a candidate is accepted when its wall
+ * nodes) are placed first and seed the queue.  Spacing h(d) from S, d the wall
+ * distance (sg_h_of); a candidate is accepted when its wall
  * distance is > wall_gap*h(d) and no node lies closer than excl*min(h(d), h_p), h_p the
  * spacing at the de-queued node.  n_cand candidates per de-queued node.  Output holds
  * the seeds first, then the fill.  Returns the total count, or -1 when cap is too small. */
-int64_t sg_advancing_front(const double *c, double r, double h_min, double h_max, double ramp,
-                           double wall_gap, double excl, int n_cand, uint64_t seed, int64_t n_seed,
-                           const double *seed_xyz, double *out, int64_t cap) {
+static int64_t sg_front(const double *c, double r, const sg_spacing *S, double wall_gap, double excl, int n_cand,
+                        uint64_t seed, int64_t n_seed, const double *seed_xyz, double *out, int64_t cap) {
+    const double h_min = S->h_min;
     if (cap < n_seed) return -1;
     sg_rng rng; sg_seed(&rng, seed);
     sg_grid G;
@@ -183,7 +196,7 @@ int64_t sg_advancing_front(const double *c, double r, double h_min, double h_max
     while (qhead < m) {
         double p[3] = {out[3 * qhead], out[3 * qhead + 1], out[3 * qhead + 2]};
         ++qhead;
-        double hp = sg_h_of(fmax(0.0, sg_sdf(c, r, p)), h_min, h_max, ramp);
+        double hp = sg_h_of(S, fmax(0.0, sg_sdf(c, r, p)));
         for (int t = 0; t < n_cand; ++t) {
             double z = 2.0 * sg_u01(&rng) - 1.0;
             double ph = 2.0 * M_PI * sg_u01(&rng);
@@ -192,7 +205,7 @@ int64_t sg_advancing_front(const double *c, double r, double h_min, double h_max
             for (int a = 0; a < 3; ++a) x[a] = sg_wrap01(x[a]);
             double d = sg_sdf(c, r, x);
             if (d <= 0.0) continue;
-            double hx = sg_h_of(d, h_min, h_max, ramp);
+            double hx = sg_h_of(S, d);
             if (d < wall_gap * hx) continue;
             if (sg_too_close(&G, out, x, excl * fmin(hx, hp))) continue;
             if (m >= cap) { free(G.head); free(G.next); return -1; }
@@ -204,4 +217,21 @@ int64_t sg_advancing_front(const double *c, double r, double h_min, double h_max
     }
     free(G.head); free(G.next);
     return m;
+}
+
+int64_t sg_advancing_front(const double *c, double r, double h_min, double h_max, double ramp,
+                           double wall_gap, double excl, int n_cand, uint64_t seed, int64_t n_seed,
+                           const double *seed_xyz, double *out, int64_t cap) {
+    sg_spacing S = {0, h_min, h_max, ramp, 1.0};
+    return sg_front(c, r, &S, wall_gap, excl, n_cand, seed, n_seed, seed_xyz, out, cap);
+}
+
+/* As sg_advancing_front with the Gaussian spacing of Eq. refinement_function
+ * (shape parameter eps); needs r < sqrt(3)/2. */
+int64_t sg_advancing_front_gauss(const double *c, double r, double h_min, double h_max, double eps,
+                                 double wall_gap, double excl, int n_cand, uint64_t seed, int64_t n_seed,
+                                 const double *seed_xyz, double *out, int64_t cap) {
+    if (!(r < 0.5 * sqrt(3.0)) || !(eps > 0.0)) return -3;
+    sg_spacing S = {1, h_min, h_max, eps, 0.5 * sqrt(3.0) - r};
+    return sg_front(c, r, &S, wall_gap, excl, n_cand, seed, n_seed, seed_xyz, out, cap);
 }

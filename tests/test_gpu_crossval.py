@@ -1,0 +1,117 @@
+"""Cross-validation of the MLBM and MNS solvers on identical nodes (the
+pointwise comparison section), through the C-ABI.
+
+* rbf_pointwise_difference against the oracle's Eq. pointwise_error evaluated on
+  the exported fields of both contexts (FP64 LBM, FP64 / compensated FP32 ACM),
+  both role orders, NaN exactly where the reference velocity is zero.
+* Argument checks: the same context twice, different node counts.
+* rbf_time_step against the oracle's time steps of both solvers.
+* Both solvers to the steady state of Eq. stopCrit on a Gaussian-refined cell:
+  the stop decision agrees with the oracle's criterion on the recorded k/d^2
+  history, and the two solutions agree in k/d^2, K and pointwise.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import gpu_or_skip, small_cell
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    return gpu_or_skip()
+
+
+@pytest.fixture(scope="module")
+def cell():
+    return small_cell()
+
+
+def _solver(rbf, case, solver, prec, steps, dx=0.5 / 14, **kw):
+    s = rbf.Solver(0)
+    s.set_case(case)
+    s.build_stencils(25)
+    s.compute_weights(solver=solver, q=19, dx=dx)
+    s.init(precision=prec, **kw)
+    s.step(steps)
+    return s
+
+
+def _check(rbf, a, b):
+    delta, dv = rbf.pointwise_difference(a, b)
+    va, vb = a.get_fields()[:, :3], b.get_fields()[:, :3]
+    want_d, want_dv = oracle.pointwise_difference(va, vb)
+    assert np.array_equal(np.isnan(delta), np.isnan(want_d))
+    ok = np.isfinite(want_d)
+    assert np.abs(dv - want_dv).max() <= 1e-13 * np.abs(want_dv).max()
+    assert np.all(np.abs(delta[ok] - want_d[ok]) <= 1e-12 * np.maximum(want_d[ok], 1e-300) + 1e-300)
+    return delta, dv
+
+
+def test_pointwise_difference_matches_definition(rbf, cell):
+    lbm = _solver(rbf, cell, rbf.RBF_SOLVER_LBM, rbf.RBF_FP64, 400, nu=1.0, tau_plus=0.8, magic=3.0 / 16.0)
+    acm = _solver(rbf, cell, rbf.RBF_SOLVER_ACM, rbf.RBF_FP64, 300, v_ref=0.01)
+    acm_c = _solver(rbf, cell, rbf.RBF_SOLVER_ACM, rbf.RBF_FP32C, 300, v_ref=0.01)
+    delta, dv = _check(rbf, lbm, acm)
+    # the MNS context holds exactly zero velocity on the wall: delta undefined there
+    wall = cell["type"] == 1
+    assert np.all(np.isnan(delta[wall])) and np.all(np.isfinite(delta[~wall]))
+    _check(rbf, acm, lbm)
+    _check(rbf, acm_c, acm)
+    # a context against a copy of itself
+    same = _solver(rbf, cell, rbf.RBF_SOLVER_ACM, rbf.RBF_FP64, 300, v_ref=0.01)
+    d0, dv0 = rbf.pointwise_difference(same, acm)
+    assert np.all(dv0 == 0.0) and np.all(d0[~wall] == 0.0)
+
+
+def test_pointwise_difference_arguments(rbf, cell):
+    a = _solver(rbf, cell, rbf.RBF_SOLVER_ACM, rbf.RBF_FP64, 1, v_ref=0.01)
+    with pytest.raises(rbf.RbfError):
+        rbf.pointwise_difference(a, a)
+    other = small_cell(n_axis=12)
+    b = _solver(rbf, other, rbf.RBF_SOLVER_ACM, rbf.RBF_FP64, 1, v_ref=0.01)
+    with pytest.raises(rbf.RbfError):
+        rbf.pointwise_difference(a, b)
+
+
+def test_time_step(rbf, cell):
+    a = _solver(rbf, cell, rbf.RBF_SOLVER_ACM, rbf.RBF_FP64, 0, v_ref=0.01)
+    idx = oracle.knn(cell["xyz"], cell["xyz"], 2)
+    h_min = np.linalg.norm(oracle.min_image(cell["xyz"][idx[:, 1]] - cell["xyz"]), axis=1).min()
+    assert abs(a.time_step() - oracle.acm_dt(h_min, 1.0)) <= 1e-15 * oracle.acm_dt(h_min, 1.0)
+    dx = 0.5 / 14
+    b = _solver(rbf, cell, rbf.RBF_SOLVER_LBM, rbf.RBF_FP64, 0, dx=dx, tau_plus=0.8, magic=3.0 / 16.0)
+    want = oracle.lbm_units(1.0, 0.8, dx, (1.0, 0.0, 0.0))["dt"]
+    assert abs(b.time_step() - want) <= 1e-15 * want
+
+
+@pytest.mark.parametrize("r,h_min", [(0.35, 0.04), (0.6526, 0.03)])
+def test_cross_validation_to_steady(rbf, r, h_min):
+    from paper_2404_14195_gb300 import crossval
+    case = synth.gaussian_cell(r=r, h_min=h_min, seed=5)
+    tol = 1e-2
+    out = crossval.cross_validate(case, n_l=25, tol=tol, window_steps=1000, max_steps=400_000, keep_fields=True)
+    for name in ("mlbm", "mns"):
+        res = out[name]
+        assert res["converged"], (name, res["steps"], res["rate"])
+        hist = res["history"]
+        window = (hist[1][0] - hist[0][0]) * res["dt"]
+        rates = [oracle.stop_criterion(hist[i][1], hist[i - 1][1], window) for i in range(1, len(hist))]
+        # stopped at the first window whose rate fell below the paper's threshold
+        assert rates[-1] < tol and all(x >= tol for x in rates[:-1]), (name, rates)
+        assert abs(res["rate"] - rates[-1]) <= 1e-12 * rates[-1]
+    # the two discretisations of the same Stokes flow agree to discretisation error
+    assert out["k_rel_diff"] < 0.05, out["k_rel_diff"]
+    assert out["K_rel_diff"] < 0.15, out["K_rel_diff"]
+    ds = out["delta_summary"]
+    assert ds["median"] < 0.1 and ds["l2_rel"] < 0.1, ds
+    # the kernel's delta matches the definition on the steady fields
+    want_d, want_dv = oracle.pointwise_difference(out["fields_mlbm"][:, :3], out["fields_mns"][:, :3])
+    ok = np.isfinite(want_d)
+    assert np.array_equal(ok, np.isfinite(out["delta"]))
+    assert np.all(np.abs(out["delta"][ok] - want_d[ok]) <= 1e-12 * want_d[ok] + 1e-300)
+    print(r, h_min, {k: out[k] for k in ("k_rel_diff", "K_rel_diff")}, ds,
+          {n: (out[n]["steps"], out[n]["k_over_d2"], out[n]["K"]) for n in ("mlbm", "mns")})
