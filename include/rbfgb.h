@@ -150,6 +150,25 @@ int rbf_set_fields(rbf_ctx *ctx, const double *uvwp);
 int rbf_lbm_get_populations(rbf_ctx *ctx, double *f);
 int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f);
 
+/* Which populations of a wall node are unknown in the streaming step and taken
+ * from the opposite direction (Eq. interpolated_bounceback_mlbm):
+ *   rule 0 (default): e_k . n > 0, n the wall normal (out of the solid; an exactly
+ *          zero product counts as known);
+ *   rule 1: the solid check of the touching-limit study (section "Permeability
+ *          and drag coefficient for various porosities"): k is unknown when the
+ *          departure point x + dx e_k' = x - dx e_k lies inside the solid, i.e.
+ *          strictly closer than r to the nearest centre of the periodic sphere
+ *          array (FP64, products and sums rounded separately, min image by rint).
+ * The rule persists in the context: set it before or after rbf_compute_weights
+ * (LBM), which recomputes the masks; rule 1 needs rbf_set_sphere.  Either call
+ * may follow rbf_init (the next step uses the new masks).  Bad rule or missing
+ * sphere -> RBF_EINVAL. */
+int rbf_lbm_set_unknown_rule(rbf_ctx *ctx, int rule);
+/* The unknown-population masks, caller's node order: bit k of mask[i] set when
+ * population k of node i is bounced back (0 for fluid nodes).  mask: host array
+ * of n uint32.  Needs LBM weights. */
+int rbf_lbm_get_unknown_mask(rbf_ctx *ctx, uint32_t *mask);
+
 /* Permeability, Eq. k_definition: probes on an m_p x m_p midpoint grid on each of
  * the planes x = 0, .2, .4, .6, .8; fluid probes interpolate v_x from their own
  * n_l nearest nodes (L = 1 weights centred at the probe), solid probes count as

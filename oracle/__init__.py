@@ -58,9 +58,9 @@ def _load():
                 "orc_rbf_weights": [I64, P, I64, P, I, I, P, I, I, I, P, P, I, P],
                 "orc_acm_run": [I64, P, P, I, P, P, I64, P, P, P, P, I, I, P, P, P, P, P],
                 "orc_lbm_collide": [I64, I, P, P, P, D, D, P, P, P],
-                "orc_lbm_stream": [I64, I, P, P, P, P, I, P, P, P, P],
-                "orc_lbm_stream_rows": [I64, I64, I, P, P, P, P, I, P, P, P, P, P],
-                "orc_lbm_run": [I64, I, P, P, P, P, P, I, P, P, D, D, P, I, P],
+                "orc_lbm_stream": [I64, I, P, P, P, P, P, I, P, P, P, P],
+                "orc_lbm_stream_rows": [I64, I64, I, P, P, P, P, P, I, P, P, P, P, P],
+                "orc_lbm_run": [I64, I, P, P, P, P, P, P, I, P, P, D, D, P, I, P],
                 "orc_lbm_macro": [I64, I, P, P, P],
                 "orc_apply": [I64, I, P, I, P, P, P],
             }
@@ -270,18 +270,30 @@ def lbm_collide(f, q: int, tau_p: float, tau_m: float, g_lb):
     return out
 
 
-def lbm_stream(fpost, q: int, case, idx, wk):
+def _mask_arg(unknown, rows=None):
+    if unknown is None:
+        return None, None
+    m = np.ascontiguousarray(unknown if rows is None else np.asarray(unknown)[rows], np.uint32)
+    return m, _p(m)
+
+
+def lbm_stream(fpost, q: int, case, idx, wk, unknown=None):
+    """Streaming step of Eq. LBM_streaming with the bounce-back of Eq.
+    interpolated_bounceback_mlbm at wall nodes; unknown: optional (n,) uint32
+    masks (bit k: population k unknown, e.g. lbm_unknown_solid), else the
+    normal rule e_k . n > 0."""
     fpost = _f64(fpost)
     n = fpost.shape[1]
     e, _, opp = velocity_set(q)
     out = np.empty_like(fpost)
+    keep, mp = _mask_arg(unknown)
     _load().orc_lbm_stream(n, q, _p(e), _p(opp), _p(np.ascontiguousarray(case["type"], np.uint8)),
-                           _p(_f64(case["normal"])), idx.shape[1], _p(_i32(idx)), _p(_f64(wk)),
+                           _p(_f64(case["normal"])), mp, idx.shape[1], _p(_i32(idx)), _p(_f64(wk)),
                            _p(fpost), _p(out))
     return out
 
 
-def lbm_stream_rows(fpost, q: int, case, rows, idx_rows, wk_rows):
+def lbm_stream_rows(fpost, q: int, case, rows, idx_rows, wk_rows, unknown=None):
     """Streaming (with bounce-back) of the selected nodes `rows` only, from the
     whole post-collision field fpost (q, n); returns (q, len(rows))."""
     fpost = _f64(fpost)
@@ -290,24 +302,62 @@ def lbm_stream_rows(fpost, q: int, case, rows, idx_rows, wk_rows):
     out = np.empty((q, len(rows)))
     typ = np.ascontiguousarray(np.asarray(case["type"])[rows], np.uint8)
     nrm = _f64(np.asarray(case["normal"])[rows])
-    _load().orc_lbm_stream_rows(len(rows), fpost.shape[1], q, _p(e), _p(opp), _p(typ), _p(nrm), idx_rows.shape[1],
+    keep, mp = _mask_arg(unknown, rows)
+    _load().orc_lbm_stream_rows(len(rows), fpost.shape[1], q, _p(e), _p(opp), _p(typ), _p(nrm), mp, idx_rows.shape[1],
                                 _p(_i32(idx_rows)), _p(rows), _p(_f64(wk_rows)), _p(fpost), _p(out))
     return out
 
 
-def lbm_run(f, q: int, case, idx, wk, tau_p: float, tau_m: float, g_lb, nsteps: int):
+def lbm_run(f, q: int, case, idx, wk, tau_p: float, tau_m: float, g_lb, nsteps: int, unknown=None):
     """nsteps of COLLIDE then STREAM (MLBM algorithm of the appendix); returns the
-    pre-collision populations f (q, n)."""
+    pre-collision populations f (q, n).  unknown: as in lbm_stream."""
     f = _f64(f).copy()
     n = f.shape[1]
     e, om, opp = velocity_set(q)
+    keep, mp = _mask_arg(unknown)
     rc = _load().orc_lbm_run(n, q, _p(e), _p(om), _p(opp),
-                             _p(np.ascontiguousarray(case["type"], np.uint8)), _p(_f64(case["normal"])),
+                             _p(np.ascontiguousarray(case["type"], np.uint8)), _p(_f64(case["normal"])), mp,
                              idx.shape[1], _p(_i32(idx)), _p(_f64(wk)), tau_p, tau_m, _p(_f64(g_lb)),
                              nsteps, _p(f))
     if rc:
         raise MemoryError("lbm_run")
     return f
+
+
+def lbm_unknown_normal(case, q: int) -> np.ndarray:
+    """Unknown-population masks of the default rule (Eq.
+    interpolated_bounceback_mlbm applied where e_k . n > 0 at wall nodes, n out
+    of the solid), as (n,) uint32 with bit k for population k."""
+    e, _, _ = velocity_set(q)
+    typ = np.asarray(case["type"])
+    nrm = np.asarray(case["normal"], np.float64)
+    mask = np.zeros(len(typ), np.uint32)
+    wall = typ == 1
+    for k in range(1, q):
+        en = (e[k, 0] * nrm[wall, 0] + e[k, 1] * nrm[wall, 1]) + e[k, 2] * nrm[wall, 2]
+        mask[wall] |= (en > 0.0).astype(np.uint32) << np.uint32(k)
+    return mask
+
+
+def lbm_unknown_solid(case, q: int, dx: float) -> np.ndarray:
+    """Unknown-population masks of the solid check used in the touching-limit
+    study (section on permeability for various porosities): at a wall node x,
+    population k is unknown when its departure point x + dx e_k' = x - dx e_k
+    lies inside the solid, i.e. strictly closer than r to the nearest sphere
+    centre of the periodic array.  (n,) uint32, bit k for population k."""
+    e, _, _ = velocity_set(q)
+    typ = np.asarray(case["type"])
+    xyz = np.asarray(case["xyz"], np.float64)
+    c = np.asarray(case["centre"], np.float64)
+    r = float(case["radius"])
+    mask = np.zeros(len(typ), np.uint32)
+    wall = typ == 1
+    for k in range(1, q):
+        p = xyz[wall] - dx * e[k]
+        d = min_image(p - c)
+        s = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        mask[wall] |= (s < r * r).astype(np.uint32) << np.uint32(k)
+    return mask
 
 
 def lbm_macro(f, q: int):

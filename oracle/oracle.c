@@ -495,7 +495,7 @@ int orc_lbm_collide(int64_t n, int q, const double *e, const double *omega, cons
  * e_k . n > 0 (departure point inside the solid) are replaced by the opposite
  * streamed population, Eq. interpolated_bounceback_mlbm. */
 int orc_lbm_stream(int64_t n, int q, const double *e, const int *opp, const uint8_t *type,
-                   const double *nrm, int n_l, const int32_t *idx, const double *wk,
+                   const double *nrm, const uint32_t *mask, int n_l, const int32_t *idx, const double *wk,
                    const double *fpost, double *f) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
@@ -510,7 +510,8 @@ int orc_lbm_stream(int64_t n, int q, const double *e, const int *opp, const uint
             const double *nn = nrm + 3 * i;
             for (int k = 1; k < q; ++k) {
                 double en = e[3 * k] * nn[0] + e[3 * k + 1] * nn[1] + e[3 * k + 2] * nn[2];
-                if (en > 0.0) f[(int64_t)k * n + i] = f[(int64_t)opp[k] * n + i];
+                int unknown = mask ? (int)((mask[i] >> k) & 1u) : en > 0.0;
+                if (unknown) f[(int64_t)k * n + i] = f[(int64_t)opp[k] * n + i];
             }
         }
     }
@@ -523,8 +524,8 @@ int orc_lbm_stream(int64_t n, int q, const double *e, const int *opp, const uint
  * post-collision field; f (q x nrows) the streamed populations of the rows.  Same
  * arithmetic as orc_lbm_stream, for checking large clouds on a sample. */
 int orc_lbm_stream_rows(int64_t nrows, int64_t n, int q, const double *e, const int *opp, const uint8_t *type,
-                        const double *nrm, int n_l, const int32_t *idx, const int64_t *rows, const double *wk,
-                        const double *fpost, double *f) {
+                        const double *nrm, const uint32_t *mask, int n_l, const int32_t *idx, const int64_t *rows,
+                        const double *wk, const double *fpost, double *f) {
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < nrows; ++r) {
         f[r] = fpost[rows[r]];
@@ -538,7 +539,8 @@ int orc_lbm_stream_rows(int64_t nrows, int64_t n, int q, const double *e, const 
             const double *nn = nrm + 3 * r;
             for (int k = 1; k < q; ++k) {
                 double en = e[3 * k] * nn[0] + e[3 * k + 1] * nn[1] + e[3 * k + 2] * nn[2];
-                if (en > 0.0) f[(int64_t)k * nrows + r] = f[(int64_t)opp[k] * nrows + r];
+                int unknown = mask ? (int)((mask[r] >> k) & 1u) : en > 0.0;
+                if (unknown) f[(int64_t)k * nrows + r] = f[(int64_t)opp[k] * nrows + r];
             }
         }
     }
@@ -548,13 +550,13 @@ int orc_lbm_stream_rows(int64_t nrows, int64_t n, int q, const double *e, const 
 /* nsteps of the MLBM algorithm of the appendix (COLLIDE over all nodes, then STREAM
  * over all nodes); f (q x n) holds the pre-collision populations in and out. */
 int orc_lbm_run(int64_t n, int q, const double *e, const double *omega, const int *opp,
-                const uint8_t *type, const double *nrm, int n_l, const int32_t *idx,
+                const uint8_t *type, const double *nrm, const uint32_t *mask, int n_l, const int32_t *idx,
                 const double *wk, double tau_p, double tau_m, const double *g, int nsteps, double *f) {
     double *fpost = malloc(sizeof(double) * (size_t)q * n);
     if (!fpost) return -1;
     for (int s = 0; s < nsteps; ++s) {
         orc_lbm_collide(n, q, e, omega, opp, tau_p, tau_m, g, f, fpost);
-        orc_lbm_stream(n, q, e, opp, type, nrm, n_l, idx, wk, fpost, f);
+        orc_lbm_stream(n, q, e, opp, type, nrm, mask, n_l, idx, wk, fpost, f);
     }
     free(fpost);
     return 0;

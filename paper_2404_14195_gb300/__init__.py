@@ -95,6 +95,8 @@ ABI = {
     "rbf_drag": (_I, [_P, _I, _P, ctypes.POINTER(_D)]),
     "rbf_pointwise_difference": (_I, [_P, _P, _P, _P]),
     "rbf_time_step": (_I, [_P, ctypes.POINTER(_D)]),
+    "rbf_lbm_set_unknown_rule": (_I, [_P, _I]),
+    "rbf_lbm_get_unknown_mask": (_I, [_P, _P]),
     "rbf_solve": (_I, [_P, ctypes.POINTER(rbf_solve_opts), ctypes.POINTER(rbf_solve_result)]),
     "rbf_last_step_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "rbf_launch_count": (_I64, [_P]),
@@ -268,6 +270,15 @@ class Solver:
         self._ck(self._L.rbf_lbm_set_populations(self._h, _ptr(a)))
 
     # -- outputs --------------------------------------------------------------
+    def lbm_set_unknown_rule(self, rule: int):
+        """0: e_k . n > 0 (default); 1: departure point inside the solid."""
+        self._ck(self._L.rbf_lbm_set_unknown_rule(self._h, int(rule)))
+
+    def lbm_get_unknown_mask(self):
+        out = np.empty(self.n, np.uint32)
+        self._ck(self._L.rbf_lbm_get_unknown_mask(self._h, _ptr(out)))
+        return out
+
     def permeability(self, m_p: int = 32):
         k, q = ctypes.c_double(), ctypes.c_double()
         self._ck(self._L.rbf_permeability(self._h, m_p, ctypes.byref(k), ctypes.byref(q)))

@@ -292,6 +292,35 @@ const char *rbf_last_error(const rbf_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t rbf_launch_count(const rbf_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
+int rbf_lbm_set_unknown_rule(rbf_ctx *ctx, int rule) {
+    if (!ctx) return RBF_EINVAL;
+    if (rule != 0 && rule != 1) return fail(ctx, RBF_EINVAL, "rbf_lbm_set_unknown_rule: rule must be 0 or 1");
+    if (rule == 1 && !ctx->has_sphere) return fail(ctx, RBF_EINVAL, "rbf_lbm_set_unknown_rule: the solid check needs rbf_set_sphere");
+    DeviceGuard dg(ctx->device);
+    ctx->lbm_rule = rule;
+    if (ctx->weights_ok && ctx->solver == RBF_SOLVER_LBM && ctx->mask.p) {
+        if (rule == 1) CK(lbm_launch_masks_solid(ctx->n, ctx->q, ctx->type.p, ctx->xyz.p, ctx->c, ctx->r, ctx->dx, ctx->mask.p, ctx->st));
+        else CK(lbm_launch_masks(ctx->n, ctx->q, ctx->type.p, ctx->nrm.p, ctx->mask.p, ctx->st));
+        ++ctx->launches;
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return RBF_OK;
+}
+
+int rbf_lbm_get_unknown_mask(rbf_ctx *ctx, uint32_t *mask) {
+    if (!ctx || !mask) return RBF_EINVAL;
+    if (!(ctx->weights_ok && ctx->solver == RBF_SOLVER_LBM && ctx->mask.p))
+        return fail(ctx, RBF_EINVAL, "rbf_lbm_get_unknown_mask: no LBM weights");
+    DeviceGuard dg(ctx->device);
+    if (ctx->stage.n * sizeof(double) < (size_t)ctx->n * sizeof(uint32_t)) CK(ctx->stage.alloc((size_t)std::max<int64_t>(4, ctx->q) * ctx->n));
+    uint32_t *tmp = reinterpret_cast<uint32_t *>(ctx->stage.p);
+    CK(launch_scatter_u32(ctx->n, ctx->perm.p, ctx->mask.p, tmp, ctx->st));
+    ++ctx->launches;
+    CK(cudaMemcpyAsync(mask, tmp, ctx->n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return RBF_OK;
+}
+
 int rbf_time_step(rbf_ctx *ctx, double *dt) {
     if (!ctx || !dt) return RBF_EINVAL;
     if (!ctx->inited) return fail(ctx, RBF_EINVAL, "rbf_time_step: not initialised");
@@ -533,8 +562,10 @@ int compute_weights_impl(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q,
     } else {
         ctx->wn32.release();
         ctx->wn64.release();
+        if (ctx->lbm_rule == 1 && !ctx->has_sphere) return fail(ctx, RBF_EINVAL, "rbf_compute_weights: the solid-check rule needs rbf_set_sphere");
         CK(ctx->mask.alloc(n));
-        CK(lbm_launch_masks(n, q, ctx->type.p, ctx->nrm.p, ctx->mask.p, ctx->st));
+        if (ctx->lbm_rule == 1) CK(lbm_launch_masks_solid(n, q, ctx->type.p, ctx->xyz.p, ctx->c, ctx->r, dx, ctx->mask.p, ctx->st));
+        else CK(lbm_launch_masks(n, q, ctx->type.p, ctx->nrm.p, ctx->mask.p, ctx->st));
         ++ctx->launches;
     }
     CK(cudaStreamSynchronize(ctx->st));

@@ -58,6 +58,7 @@ struct rbf_ctx {
     bool weights_ok = false;
     int solver = -1, q = 0, phs_k = 0, mono_m = 0, n_ops = 0;
     double dx = 0.0, h_min = 0.0;
+    int lbm_rule = 0;  // unknown populations at wall nodes: 0 e_k . n > 0, 1 departure point in the solid
     DevArr<double> w64, wgb64, wgw64, delta;
     DevArr<float> ws32, wn32;
     DevArr<double> ws64, wn64;

@@ -83,6 +83,34 @@ __global__ void k_lbm_masks(int64_t n, const uint8_t *__restrict__ type, const d
     mask[i] = m;
 }
 
+// Solid-check rule of the touching-limit study: at a wall node x, bit k is set
+// when the departure point x + dx e_k' = x - dx e_k lies inside the solid, i.e.
+// closer than r to the nearest centre of the periodic sphere array.  Products and
+// sums in round-to-nearest without contraction, so the decision is the same
+// as an FP64 evaluation in this order.
+template <int Q>
+__global__ void k_lbm_masks_solid(int64_t n, const uint8_t *__restrict__ type, const double *__restrict__ xyz,
+                                  double c0, double c1, double c2, double r, double dx, uint32_t *mask) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t m = 0;
+    if (type[i]) {
+        const double c[3] = {c0, c1, c2};
+        const double r2 = __dmul_rn(r, r);
+        for (int k = 1; k < Q; ++k) {
+            double d[3];
+            for (int a = 0; a < 3; ++a) {
+                const double p = __dsub_rn(xyz[3 * i + a], __dmul_rn(dx, (double)VSet<Q>::e(k, a)));
+                const double v = __dsub_rn(p, c[a]);
+                d[a] = __dsub_rn(v, rint(v));
+            }
+            const double s = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+            if (s < r2) m |= 1u << k;
+        }
+    }
+    mask[i] = m;
+}
+
 // TRT collision of one node in shifted variables; f[] in, f[] out (post-collision)
 template <typename T, int Q>
 __device__ __forceinline__ void trt_collide(T (&f)[Q], T tp_inv, T tm_inv, T gx, T gy, T gz) {
@@ -481,6 +509,26 @@ cudaError_t lbm_launch_masks(int64_t n, int q, const uint8_t *type, const double
     if (q == 19) k_lbm_masks<19><<<g, 256, 0, st>>>(n, type, nrm, mask);
     else if (q == 15) k_lbm_masks<15><<<g, 256, 0, st>>>(n, type, nrm, mask);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t lbm_launch_masks_solid(int64_t n, int q, const uint8_t *type, const double *xyz, const double c[3], double r,
+                                  double dx, uint32_t *mask, cudaStream_t st) {
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (q == 19) k_lbm_masks_solid<19><<<g, 256, 0, st>>>(n, type, xyz, c[0], c[1], c[2], r, dx, mask);
+    else if (q == 15) k_lbm_masks_solid<15><<<g, 256, 0, st>>>(n, type, xyz, c[0], c[1], c[2], r, dx, mask);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_u32(int64_t n, const int32_t *__restrict__ perm, const uint32_t *__restrict__ in,
+                              uint32_t *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = in[i];
+}
+cudaError_t launch_scatter_u32(int64_t n, const int32_t *perm, const uint32_t *in, uint32_t *out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_scatter_u32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, perm, in, out);
     return cudaGetLastError();
 }
 

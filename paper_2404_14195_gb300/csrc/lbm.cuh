@@ -50,6 +50,11 @@ cudaError_t lbm_launch_pack_f64(int64_t nc, int q, int n_l, const double *w, dou
 template <typename T>
 cudaError_t lbm_launch_init(const LbmArgs<T> &a, int q, cudaStream_t st);
 cudaError_t lbm_launch_masks(int64_t n, int q, const uint8_t *type, const double *nrm, uint32_t *mask, cudaStream_t st);
+// solid-check unknown-population masks (departure point inside the sphere array)
+cudaError_t lbm_launch_masks_solid(int64_t n, int q, const uint8_t *type, const double *xyz, const double c[3], double r,
+                                  double dx, uint32_t *mask, cudaStream_t st);
+// out[perm[i]] = in[i]
+cudaError_t launch_scatter_u32(int64_t n, const int32_t *perm, const uint32_t *in, uint32_t *out, cudaStream_t st);
 template <typename T>
 cudaError_t lbm_launch_export(int64_t n, int64_t npad, int layout, int q, const T *f, const int32_t *perm, double *out,
                               cudaStream_t st);
