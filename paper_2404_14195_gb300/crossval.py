@@ -61,12 +61,26 @@ def run_to_steady(s: Solver, tol: float = 1e-2, window_steps: int = 10_000, max_
                 wall_s=time.perf_counter() - t0)
 
 
+def auto_v_ref(h_min: float, nu: float = 1.0, beta: float = 10.0, cfl: float = 0.1, courant: float = 0.01) -> float:
+    """v_ref that puts the artificial sound speed C = beta v_ref at an acoustic
+    Courant number C dt / h_min = `courant`, with dt = cfl h_min^2 / (2 nu) the
+    MNS time step (h_min the smallest internodal distance).  A build choice, not
+    the paper's: the steady state does not depend on C, and a C this large lets
+    the pressure relax within ~10^5 steps also in low-porosity cells (0.01 is
+    about a tenth of the Courant number at which r = 0.6526 went unstable)."""
+    return courant * 2.0 * nu / (beta * cfl * h_min)
+
+
 def _solver(case, n_l, k, m, solver, q, dx, init_kw, device):
     s = Solver(device)
     s.set_case(case)
     s.build_stencils(n_l)
-    s.compute_weights(k=k, m=m, solver=solver, q=q, dx=dx)
-    s.init(**init_kw)
+    rep = s.compute_weights(k=k, m=m, solver=solver, q=q, dx=dx)
+    kw = dict(init_kw)
+    if kw.get("v_ref") == "auto":
+        kw["v_ref"] = auto_v_ref(rep["h_min"], kw.get("nu", 1.0), kw.get("beta", 10.0))
+    s.init(**kw)
+    s.v_ref_used = kw.get("v_ref")
     return s
 
 
@@ -106,7 +120,7 @@ def delta_summary(case, delta, dv, v_b_speed, levels=(1.0, 0.25, 0.1, 0.05, 0.01
 
 def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx: float | None = None,
                    tau_plus: float = 1.0, magic: float = 1.0, nu: float = 1.0, g=(1.0, 0.0, 0.0),
-                   v_ref: float = 0.01, beta: float = 10.0, precision_lbm: int = RBF_FP64,
+                   v_ref: float | str = 0.01, beta: float = 10.0, precision_lbm: int = RBF_FP64,
                    precision_acm: int = RBF_FP64, tol: float = 1e-2, window_steps: int = 10_000,
                    window_steps_lbm: int | None = None, max_steps: int = 2_000_000, m_p: int = 32,
                    device: int = 0, keep_fields: bool = False, unknown_rule: int = 0, n_l_lbm: int | None = None,
@@ -123,7 +137,8 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
     MNS_C.  It does not change the steady state, only how fast the pressure
     relaxes: in low-porosity cells (r = 0.6526) the default 0.01 leaves a
     transient so slow that the rate criterion of Eq. stopCrit fires long before
-    k/d^2 has settled, and a v_ref of order 10 is needed.
+    k/d^2 has settled, and a v_ref of order 10 is needed.  v_ref = "auto" takes
+    auto_v_ref of the cell's smallest internodal distance.
     Returns a dict with per-solver results, the delta summary, the line profile
     and (keep_fields) the velocity fields."""
     dx = 0.5 * case["h_min"] if dx is None else dx
@@ -146,6 +161,8 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
         kk, qq = s.permeability(m_p)
         F, K = s.drag(m_p)
         r.update(k_over_d2=kk, q=qq, F=F, K=K)
+        if name == "mns":
+            r["v_ref"] = s.v_ref_used
         out[name] = r
     delta, dv = pointwise_difference(lbm, acm)
     fa, fb = lbm.get_fields(), acm.get_fields()
@@ -199,7 +216,7 @@ def main(argv=None):
     ap.add_argument("--magic", type=float, default=1.0)
     ap.add_argument("--n-l-lbm", type=int, default=None)
     ap.add_argument("--unknown-rule", type=int, default=0, choices=(0, 1))
-    ap.add_argument("--v-ref", type=float, default=0.01)
+    ap.add_argument("--v-ref", default="0.01", help='a number, or "auto"')
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-2)
     ap.add_argument("--window", type=int, default=10_000)
@@ -212,7 +229,7 @@ def main(argv=None):
     out = cross_validate(case, n_l=a.n_l, q=a.q, tau_plus=a.tau_plus, magic=a.magic, tol=a.tol,
                          window_steps=a.window, max_steps=a.max_steps, precision_lbm=prec[a.precision_lbm],
                          precision_acm=prec[a.precision_acm], unknown_rule=a.unknown_rule, n_l_lbm=a.n_l_lbm,
-                         v_ref=a.v_ref, tune=a.tune)
+                         v_ref=a.v_ref if a.v_ref == "auto" else float(a.v_ref), tune=a.tune)
     line = out.pop("line")
     step = max(1, len(line["x"]) // 64)
     out["line"] = {k: v[::step] for k, v in line.items() if k != "node"}

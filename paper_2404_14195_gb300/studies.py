@@ -1,0 +1,190 @@
+"""Parameter studies of the paper around the two solvers: the porosity sweep
+(section "Permeability and drag coefficient for various porosities"), the
+node-placement spread over seeds ("Node placement sensitivity"), the
+refinement-parameter and stencil-size studies ("Influence of the refinement
+parameters and the stencil size", Eq. refinement_error) and the grid
+convergence index of the appendix (Eqs. gci_convergence_study,
+relative_error_convergence_study, pairwise_relative_error_convergence_study).
+
+Orchestration only: every solve runs through `crossval.cross_validate` or
+`crossval.run_to_steady` in the library's kernels; the host evaluates the
+scalar formulas of the studies.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import RBF_FP32C, RBF_FP64
+from . import crossval
+
+# the radii of the paper's porosity sweep run over r in [0.04, 0.69]
+SWEEP_RADII = (0.04, 0.062, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4, 0.45, 0.49, 0.55, 0.6, 0.6526, 0.69)
+
+
+# ---------------------------------------------------------------- GCI
+def apparent_order(h, X, h_ref: float | None = None) -> float:
+    """p_X of the appendix: slope of the least-squares line through
+    (log h, log e_X(h)) with e_X(h) = |X(h) - X(h_ref)| / X(h_ref) (Eq.
+    relative_error_convergence_study), h_ref the finest h by default; the point
+    h_ref itself (e = 0) is left out."""
+    h = np.asarray(h, np.float64)
+    X = np.asarray(X, np.float64)
+    iref = int(np.argmin(h)) if h_ref is None else int(np.nonzero(h == h_ref)[0][0])
+    e = np.abs(X - X[iref]) / abs(X[iref])
+    use = (np.arange(len(h)) != iref) & (e > 0)
+    if use.sum() < 2:
+        raise ValueError("apparent_order needs two coarser points with a nonzero error")
+    slope, _ = np.polyfit(np.log(h[use]), np.log(e[use]), 1)
+    return float(slope)
+
+
+def gci(h, X, F_s: float = 1.3, h_ref: float | None = None, p: float | None = None):
+    """Grid convergence index of Eq. gci_convergence_study for every pair of
+    successive discretisations, assigned to the finer one of the pair:
+    GCI = F_s |eps| / (r^p - 1), eps = |X_coarser - X_finer| / X_finer (Eq.
+    pairwise_relative_error_convergence_study), r = h_coarser / h_finer > 1, p
+    from apparent_order unless given.  Returns (p, {h_finer: GCI})."""
+    h = np.asarray(h, np.float64)
+    X = np.asarray(X, np.float64)
+    o = np.argsort(-h)  # coarse to fine
+    h, X = h[o], X[o]
+    if p is None:
+        p = apparent_order(h, X, h_ref)
+    out = {}
+    for i in range(1, len(h)):
+        r = h[i - 1] / h[i]
+        eps = abs(X[i - 1] - X[i]) / abs(X[i])
+        out[float(h[i])] = F_s * eps / (r ** p - 1.0)
+    return p, out
+
+
+def refinement_error(K, K_ref) -> float:
+    """E of Eq. refinement_error: |K - K_ref| / K_ref, K_ref the value on the
+    uniform discretisation (h_max / h_min = 1)."""
+    return abs(K - K_ref) / abs(K_ref)
+
+
+# ---------------------------------------------------------------- runs
+def _run(r, h_min, seed=2, h_ratio=2.0, eps=0.295, n_l=25, v_ref="auto", **kw):
+    import synth
+    case = synth.gaussian_cell(r=r, h_min=h_min, h_max=h_ratio * h_min, eps=eps, seed=seed)
+    t = time.perf_counter()
+    out = crossval.cross_validate(case, n_l=n_l, v_ref=v_ref, **kw)
+    res = dict(r=r, h_min=h_min, seed=seed, h_ratio=h_ratio, eps=eps, n_l=n_l, n=case.n,
+               wall_s=time.perf_counter() - t)
+    for nm in ("mlbm", "mns"):
+        x = out[nm]
+        res[nm] = dict(k=x["k_over_d2"], K=x["K"], steps=x["steps"], converged=x["converged"],
+                       time=x["time"], wall_s=x["wall_s"], v_ref=x.get("v_ref"))
+    res["delta_median"] = out["delta_summary"]["median"]
+    res["delta_l2"] = out["delta_summary"]["l2_rel"]
+    return res
+
+
+def porosity_sweep(radii=SWEEP_RADII, h_min: float = 0.02, seed: int = 2, **kw):
+    """k/d^2 and K of both solvers over the radii (one cross-validation per
+    radius, same nodes for both solvers)."""
+    return [_run(r, h_min, seed=seed, **kw) for r in radii]
+
+
+def seed_spread(radii, h_min: float = 0.02, seeds=(1, 2, 3, 4, 5), **kw):
+    """Node-placement sensitivity: per radius, the standard deviation of k/d^2
+    and K over node sets that differ only in the generator's seed, normalised
+    by the mean (only converged runs count)."""
+    out = []
+    for r in radii:
+        runs = [_run(r, h_min, seed=s, **kw) for s in seeds]
+        row = dict(r=r, runs=runs)
+        for nm in ("mlbm", "mns"):
+            for q in ("k", "K"):
+                v = np.array([x[nm][q] for x in runs if x[nm]["converged"] and np.isfinite(x[nm][q])])
+                row[f"{nm}_{q}_spread"] = float(v.std(ddof=1) / v.mean()) if len(v) > 1 else float("nan")
+                row[f"{nm}_{q}_n"] = int(len(v))
+        out.append(row)
+    return out
+
+
+def convergence_study(r, h_list, **kw):
+    """Both solvers at each h_min, then p and GCI of k/d^2 and K per solver."""
+    runs = [_run(r, h, **kw) for h in h_list]
+    res = dict(r=r, runs=runs)
+    hs = [x["h_min"] for x in runs]
+    for nm in ("mlbm", "mns"):
+        for q in ("k", "K"):
+            vals = [x[nm][q] for x in runs]
+            try:
+                p, g = gci(hs, vals)
+            except ValueError:
+                p, g = float("nan"), {}
+            res[f"{nm}_{q}_p"] = p
+            res[f"{nm}_{q}_gci"] = g
+    return res
+
+
+def refinement_parameter_study(r, h_min: float = 0.01, ratios=(1.0, 2.0, 3.0, 4.0), eps_list=(0.1, 0.2, 0.3),
+                               **kw):
+    """E(h_max/h_min, eps) of Eq. refinement_error for both solvers, against the
+    uniform discretisation (ratio 1)."""
+    ref = _run(r, h_min, h_ratio=1.0, eps=1.0, **kw)
+    rows = []
+    for ratio in ratios:
+        if ratio == 1.0:
+            continue
+        for e in eps_list:
+            x = _run(r, h_min, h_ratio=ratio, eps=e, **kw)
+            for nm in ("mlbm", "mns"):
+                x[nm]["E"] = refinement_error(x[nm]["K"], ref[nm]["K"]) if x[nm]["converged"] else float("nan")
+            rows.append(x)
+    return dict(r=r, reference=ref, rows=rows)
+
+
+def stencil_size_study(r, n_l_list=(15, 20, 25, 30, 35, 40), h_min: float = 0.01, h_ratio: float = 3.0,
+                       eps: float = 0.3, **kw):
+    """K of both solvers against the stencil size N_L (the paper's stencil-size
+    figure: r = 0.6526, h_max / h_min = 3)."""
+    return [_run(r, h_min, h_ratio=h_ratio, eps=eps, n_l=n, **kw) for n in n_l_list]
+
+
+def main(argv=None):
+    """Command line: one study, JSON to stdout (and --out)."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("study", choices=("porosity", "spread", "convergence", "refinement", "stencil"))
+    ap.add_argument("--radii", default=None, help="comma-separated radii")
+    ap.add_argument("--h-min", type=float, default=0.02)
+    ap.add_argument("--h-list", default="0.028,0.02,0.014,0.01")
+    ap.add_argument("--seeds", default="1,2,3,4,5")
+    ap.add_argument("--n-l-list", default="15,20,25,30,35,40")
+    ap.add_argument("--window", type=int, default=10_000)
+    ap.add_argument("--max-steps", type=int, default=4_000_000)
+    ap.add_argument("--precision-acm", choices=("fp64", "fp32c"), default="fp32c")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    radii = tuple(float(x) for x in a.radii.split(",")) if a.radii else SWEEP_RADII
+    kw = dict(window_steps=a.window, max_steps=a.max_steps, tune=True,
+              precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64, precision_lbm=RBF_FP64)
+    t = time.perf_counter()
+    if a.study == "porosity":
+        res = porosity_sweep(radii, a.h_min, **kw)
+    elif a.study == "spread":
+        res = seed_spread(radii, a.h_min, seeds=tuple(int(x) for x in a.seeds.split(",")), **kw)
+    elif a.study == "convergence":
+        res = [convergence_study(r, [float(x) for x in a.h_list.split(",")], **kw) for r in radii]
+    elif a.study == "refinement":
+        res = [refinement_parameter_study(r, a.h_min, **kw) for r in radii]
+    else:
+        res = [stencil_size_study(r, tuple(int(x) for x in a.n_l_list.split(",")), a.h_min, **kw) for r in radii]
+    txt = json.dumps(crossval._jsonable(dict(study=a.study, args=vars(a), wall_s=time.perf_counter() - t,
+                                             result=res)))
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(txt + "\n")
+
+
+if __name__ == "__main__":
+    main()

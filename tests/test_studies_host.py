@@ -1,0 +1,48 @@
+"""Host arithmetic of the parameter studies (no GPU): the grid convergence
+index of the appendix and the refinement error.
+
+* The apparent order p is recovered exactly from errors that follow A h^p.
+* Richardson's property: for X(h) = X_inf + c h^p and the true p, GCI / F_s on
+  the finer grid of a pair equals the true relative error |X_fine - X_inf| /
+  X_fine, whatever the refinement ratio.
+* GCI belongs to the finer grid of each successive pair, in any input order.
+"""
+import numpy as np
+import pytest
+
+from paper_2404_14195_gb300 import studies
+
+
+def test_apparent_order_exact_power_law():
+    h = np.array([0.02, 0.014, 0.01, 0.007, 0.005])
+    for p in (1.0, 1.7, 2.5):
+        X = 0.3 * (1.0 + 40.0 * h ** p)
+        X[-1] = 0.3  # the reference value: e = A h^p exactly for the others
+        assert abs(studies.apparent_order(h, X) - p) < 1e-10
+
+
+@pytest.mark.parametrize("p,h", [(2.0, [0.02, 0.01]), (1.5, [0.02, 0.014, 0.01, 0.007]), (3.0, [0.05, 0.02])])
+def test_gci_richardson_property(p, h):
+    X_inf, c = 1.25, -7.0
+    h = np.array(h)
+    X = X_inf + c * h ** p
+    _, g = studies.gci(h, X, F_s=1.3, p=p)
+    for i in range(1, len(h)):
+        fine = X[i]
+        assert abs(g[float(h[i])] / 1.3 - abs(fine - X_inf) / abs(fine)) < 1e-12
+
+
+def test_gci_pairs_go_to_the_finer_grid():
+    h = [0.01, 0.02, 0.014]  # any order
+    X = [1.0, 1.2, 1.1]
+    _, g = studies.gci(h, X, p=2.0)
+    assert sorted(g) == [0.01, 0.014]
+    # pair (0.02, 0.014): eps = 0.1 / 1.1, r = 0.02 / 0.014
+    assert abs(g[0.014] - 1.3 * (0.1 / 1.1) / ((0.02 / 0.014) ** 2 - 1.0)) < 1e-15
+    with pytest.raises(ValueError):
+        studies.apparent_order([0.02, 0.01], [1.1, 1.0])
+
+
+def test_refinement_error():
+    assert studies.refinement_error(1.1, 1.0) == pytest.approx(0.1)
+    assert studies.refinement_error(0.9, 1.0) == pytest.approx(0.1)
