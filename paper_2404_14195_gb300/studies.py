@@ -83,10 +83,18 @@ def _run(r, h_min, seed=2, h_ratio=2.0, eps=0.295, n_l=25, v_ref="auto", **kw):
     return res
 
 
-def porosity_sweep(radii=SWEEP_RADII, h_min: float = 0.02, seed: int = 2, **kw):
+def porosity_sweep(radii=SWEEP_RADII, h_min: float = 0.02, seed: int = 2, solid_check_above: float | None = None,
+                   **kw):
     """k/d^2 and K of both solvers over the radii (one cross-validation per
-    radius, same nodes for both solvers)."""
-    return [_run(r, h_min, seed=seed, **kw) for r in radii]
+    radius, same nodes for both solvers).  solid_check_above: radius from which
+    the MLBM uses the solid-check bounce-back rule (the paper switches to it
+    near and past the touching limit)."""
+    out = []
+    for r in radii:
+        rule = 1 if (solid_check_above is not None and r >= solid_check_above) else 0
+        out.append(_run(r, h_min, seed=seed, unknown_rule=rule, **kw))
+        out[-1]["unknown_rule"] = rule
+    return out
 
 
 def seed_spread(radii, h_min: float = 0.02, seeds=(1, 2, 3, 4, 5), **kw):
@@ -162,6 +170,7 @@ def main(argv=None):
     ap.add_argument("--window", type=int, default=10_000)
     ap.add_argument("--max-steps", type=int, default=4_000_000)
     ap.add_argument("--precision-acm", choices=("fp64", "fp32c"), default="fp32c")
+    ap.add_argument("--solid-check-above", type=float, default=None)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     radii = tuple(float(x) for x in a.radii.split(",")) if a.radii else SWEEP_RADII
@@ -169,7 +178,7 @@ def main(argv=None):
               precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64, precision_lbm=RBF_FP64)
     t = time.perf_counter()
     if a.study == "porosity":
-        res = porosity_sweep(radii, a.h_min, **kw)
+        res = porosity_sweep(radii, a.h_min, solid_check_above=a.solid_check_above, **kw)
     elif a.study == "spread":
         res = seed_spread(radii, a.h_min, seeds=tuple(int(x) for x in a.seeds.split(",")), **kw)
     elif a.study == "convergence":

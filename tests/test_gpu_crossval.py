@@ -98,7 +98,7 @@ def test_time_step(rbf, cell):
 # slowly that the rate criterion stops it on a transient ~20x away from the
 # steady k/d^2.
 @pytest.mark.parametrize("r,h_min,v_ref,bars", [(0.35, 0.04, 0.01, (0.05, 0.15, 0.1, 0.1)),
-                                                (0.6526, 0.02, 10.0, (0.12, 0.12, None, 0.2))])
+                                                (0.6526, 0.02, 10.0, (0.12, 0.12, None, 0.25))])
 def test_cross_validation_to_steady(rbf, r, h_min, v_ref, bars):
     from paper_2404_14195_gb300 import crossval
     case = synth.gaussian_cell(r=r, h_min=h_min, seed=5)
