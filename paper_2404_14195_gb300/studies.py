@@ -66,6 +66,33 @@ def refinement_error(K, K_ref) -> float:
     return abs(K - K_ref) / abs(K_ref)
 
 
+# ---------------------------------------------------------------- ranks
+def dist_env():
+    """(dist or None, rank, world size, local rank) from the torchrun environment.
+    With more than one rank, a gloo process group carries the results to every
+    rank; the solves themselves share nothing (one independent cell per run)."""
+    import os
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("gloo")
+    return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def run_sharded(fn, items, dist=None, rank: int = 0, world: int = 1):
+    """fn(item) for the items i with i % world == rank, then every rank gets all
+    results in item order (all_gather_object of the per-rank lists)."""
+    mine = [(i, fn(x)) for i, x in enumerate(items) if i % world == rank]
+    if dist is None or world == 1:
+        return [r for _, r in mine]
+    parts = [None] * world
+    dist.all_gather_object(parts, mine)
+    merged = sorted((p for part in parts for p in part), key=lambda p: p[0])
+    return [r for _, r in merged]
+
+
 # ---------------------------------------------------------------- runs
 def _run(r, h_min, seed=2, h_ratio=2.0, eps=0.295, n_l=25, v_ref="auto", **kw):
     import synth
@@ -91,26 +118,29 @@ def _run(r, h_min, seed=2, h_ratio=2.0, eps=0.295, n_l=25, v_ref="auto", **kw):
 
 
 def porosity_sweep(radii=SWEEP_RADII, h_min: float = 0.02, seed: int = 2, solid_check_above: float | None = None,
-                   **kw):
+                   _ranks=(), **kw):
     """k/d^2 and K of both solvers over the radii (one cross-validation per
     radius, same nodes for both solvers).  solid_check_above: radius from which
     the MLBM uses the solid-check bounce-back rule (the paper switches to it
-    near and past the touching limit)."""
-    out = []
-    for r in radii:
+    near and past the touching limit).  _ranks: (dist, rank, world) to spread
+    the radii over ranks (run_sharded)."""
+    def one(r):
         rule = 1 if (solid_check_above is not None and r >= solid_check_above) else 0
-        out.append(_run(r, h_min, seed=seed, unknown_rule=rule, **kw))
-        out[-1]["unknown_rule"] = rule
-    return out
+        x = _run(r, h_min, seed=seed, unknown_rule=rule, **kw)
+        x["unknown_rule"] = rule
+        return x
+    return run_sharded(one, list(radii), *_ranks)
 
 
-def seed_spread(radii, h_min: float = 0.02, seeds=(1, 2, 3, 4, 5), **kw):
+def seed_spread(radii, h_min: float = 0.02, seeds=(1, 2, 3, 4, 5), _ranks=(), **kw):
     """Node-placement sensitivity: per radius, the standard deviation of k/d^2
     and K over node sets that differ only in the generator's seed, normalised
     by the mean (only converged runs count)."""
+    pairs = [(r, sd) for r in radii for sd in seeds]
+    allruns = run_sharded(lambda p: _run(p[0], h_min, seed=p[1], **kw), pairs, *_ranks)
     out = []
-    for r in radii:
-        runs = [_run(r, h_min, seed=s, **kw) for s in seeds]
+    for i, r in enumerate(radii):
+        runs = allruns[i * len(seeds):(i + 1) * len(seeds)]
         row = dict(r=r, runs=runs)
         for nm in ("mlbm", "mns"):
             for q in ("k", "K"):
@@ -163,7 +193,9 @@ def stencil_size_study(r, n_l_list=(15, 20, 25, 30, 35, 40), h_min: float = 0.01
 
 
 def main(argv=None):
-    """Command line: one study, JSON to stdout (and --out)."""
+    """Command line: one study, JSON to stdout (and --out).  Under torchrun the
+    porosity sweep and the seed spread spread their runs over the ranks, one GPU
+    per rank (LOCAL_RANK), and rank 0 prints the merged result."""
     import argparse
     import json
 
@@ -181,21 +213,25 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     radii = tuple(float(x) for x in a.radii.split(",")) if a.radii else SWEEP_RADII
-    kw = dict(window_steps=a.window, max_steps=a.max_steps, tune=True,
+    dist, rank, world, local = dist_env()
+    ranks = (dist, rank, world)
+    kw = dict(window_steps=a.window, max_steps=a.max_steps, tune=True, device=local,
               precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64, precision_lbm=RBF_FP64)
     t = time.perf_counter()
     if a.study == "porosity":
-        res = porosity_sweep(radii, a.h_min, solid_check_above=a.solid_check_above, **kw)
+        res = porosity_sweep(radii, a.h_min, solid_check_above=a.solid_check_above, _ranks=ranks, **kw)
     elif a.study == "spread":
-        res = seed_spread(radii, a.h_min, seeds=tuple(int(x) for x in a.seeds.split(",")), **kw)
+        res = seed_spread(radii, a.h_min, seeds=tuple(int(x) for x in a.seeds.split(",")), _ranks=ranks, **kw)
     elif a.study == "convergence":
         res = [convergence_study(r, [float(x) for x in a.h_list.split(",")], **kw) for r in radii]
     elif a.study == "refinement":
         res = [refinement_parameter_study(r, a.h_min, **kw) for r in radii]
     else:
         res = [stencil_size_study(r, tuple(int(x) for x in a.n_l_list.split(",")), a.h_min, **kw) for r in radii]
-    txt = json.dumps(crossval._jsonable(dict(study=a.study, args=vars(a), wall_s=time.perf_counter() - t,
-                                             result=res)))
+    txt = json.dumps(crossval._jsonable(dict(study=a.study, args=vars(a), ranks=world,
+                                             wall_s=time.perf_counter() - t, result=res)))
+    if rank != 0:
+        return
     print(txt)
     if a.out:
         with open(a.out, "w") as f:

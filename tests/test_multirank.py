@@ -51,3 +51,40 @@ def test_single_process_needs_no_collective():
     import bench
     assert bench._max_over_ranks(3.5, None) == 3.5
     assert bench.whole_job_rate(10, 1, 2.0) == 5.0
+
+
+def _study_rank(rank, world, port, out_dir):
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    from paper_2404_14195_gb300 import studies
+    dist, r, ws, local = studies.dist_env()
+    assert (r, ws, local) == (rank, world, rank)
+    seen = []
+
+    def fn(x):
+        seen.append(x)
+        return dict(x=x, rank=rank)
+    res = studies.run_sharded(fn, [0.1, 0.2, 0.3, 0.4, 0.5], dist, r, ws)
+    with open(os.path.join(out_dir, f"study{rank}.txt"), "w") as f:
+        f.write(repr((seen, res)) + "\n")
+    dist.destroy_process_group()
+
+
+def test_studies_shard_runs_over_gloo_ranks(tmp_path):
+    """The studies' runs (independent cells) go round-robin to the ranks; every
+    rank ends with all results in item order."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    mp.start_processes(_study_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    import ast
+    got = [ast.literal_eval(open(tmp_path / f"study{r}.txt").read()) for r in (0, 1)]
+    assert got[0][0] == [0.1, 0.3, 0.5] and got[1][0] == [0.2, 0.4]
+    want = [dict(x=x, rank=i % 2) for i, x in enumerate([0.1, 0.2, 0.3, 0.4, 0.5])]
+    assert got[0][1] == want and got[1][1] == want
+
+
+def test_studies_single_process():
+    sys.path.insert(0, ROOT)
+    from paper_2404_14195_gb300 import studies
+    assert studies.run_sharded(lambda x: 2 * x, [1, 2, 3]) == [2, 4, 6]
