@@ -80,8 +80,7 @@ def _solver(case, n_l, k, m, solver, q, dx, init_kw, device):
     if kw.get("v_ref") == "auto":
         kw["v_ref"] = auto_v_ref(rep["h_min"], kw.get("nu", 1.0), kw.get("beta", 10.0))
     s.init(**kw)
-    s.v_ref_used = kw.get("v_ref")
-    return s
+    return s, kw.get("v_ref")
 
 
 def line_profile(case, v_a, v_b, half_width: float | None = None, y0: float = 0.5, z0: float = 0.5):
@@ -143,10 +142,10 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
     and (keep_fields) the velocity fields."""
     dx = 0.5 * case["h_min"] if dx is None else dx
     t0 = time.perf_counter()
-    lbm = _solver(case, n_l_lbm or n_l, k, m, RBF_SOLVER_LBM, q, dx,
-                  dict(precision=precision_lbm, nu=nu, g=g, tau_plus=tau_plus, magic=magic), device)
-    acm = _solver(case, n_l, k, m, RBF_SOLVER_ACM, q, 0.0,
-                  dict(precision=precision_acm, nu=nu, g=g, v_ref=v_ref, beta=beta), device)
+    lbm, _ = _solver(case, n_l_lbm or n_l, k, m, RBF_SOLVER_LBM, q, dx,
+                     dict(precision=precision_lbm, nu=nu, g=g, tau_plus=tau_plus, magic=magic), device)
+    acm, v_ref_used = _solver(case, n_l, k, m, RBF_SOLVER_ACM, q, 0.0,
+                              dict(precision=precision_acm, nu=nu, g=g, v_ref=v_ref, beta=beta), device)
     setup_s = time.perf_counter() - t0
     out = dict(n=case.n, n_wall=int((np.asarray(case["type"]) == 1).sum()), dx=dx, setup_s=setup_s)
     for name, s, w in (("mlbm", lbm, window_steps_lbm or window_steps), ("mns", acm, window_steps)):
@@ -162,7 +161,7 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
         F, K = s.drag(m_p)
         r.update(k_over_d2=kk, q=qq, F=F, K=K)
         if name == "mns":
-            r["v_ref"] = s.v_ref_used
+            r["v_ref"] = v_ref_used
         out[name] = r
     delta, dv = pointwise_difference(lbm, acm)
     fa, fb = lbm.get_fields(), acm.get_fields()
