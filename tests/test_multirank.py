@@ -31,6 +31,7 @@ def _rank_main(rank, world, port, out_dir):
     seconds = [0.8, 1.25][rank]  # rank 1 is the slow one
     tmax = bench._max_over_ranks(seconds, dist)
     rate = bench.whole_job_rate(1000, ws, tmax)
+    assert bench._sum_over_ranks([100.0, 250.0][rank], dist) == 350.0
     with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
         f.write(f"{tmax} {rate}\n")
     dist.destroy_process_group()
@@ -88,3 +89,16 @@ def test_studies_single_process():
     sys.path.insert(0, ROOT)
     from paper_2404_14195_gb300 import studies
     assert studies.run_sharded(lambda x: 2 * x, [1, 2, 3]) == [2, 4, 6]
+
+
+def test_batch_cells_are_disjoint_per_rank():
+    """Rank r's cells of the batched workload are the r-th block of one seeded
+    sequence: rank 0 keeps the one-GPU cells, the ranks share no cell."""
+    sys.path.insert(0, ROOT)
+    import bench
+    one = bench.config3_jobs(4)
+    two = bench.config3_jobs(8)
+    assert bench.config3_jobs(4, rank=0) == one == two[:4]
+    assert bench.config3_jobs(4, rank=1) == two[4:]
+    seeds = [j[2] for j in bench.config3_jobs(4, rank=0) + bench.config3_jobs(4, rank=1)]
+    assert len(set(seeds)) == 8
