@@ -192,6 +192,48 @@ def stencil_size_study(r, n_l_list=(15, 20, 25, 30, 35, 40), h_min: float = 0.01
     return [_run(r, h_min, h_ratio=h_ratio, eps=eps, n_l=n, **kw) for n in n_l_list]
 
 
+def single_solver_trace(r, h_min, solver: str, chunk: int, chunks: int, seed: int = 2, n_l: int = 25,
+                        v_ref=0.01, unknown_rule: int = 0, precision: int = RBF_FP64, tune: bool = True,
+                        device: int = 0):
+    """One solver alone on a Gaussian-refined cell, stepped in `chunks` chunks of
+    `chunk` steps from rest: (steps, k/d^2, F_x) after every chunk, stopping at
+    the first non-finite k.  For transients that the rate criterion of Eq.
+    stopCrit cannot see (the MNS pressure relaxation at low porosity, reading its
+    dependence on v_ref) and for MLBM stability under the two bounce-back rules."""
+    import synth
+    from . import RBF_SOLVER_ACM, RBF_SOLVER_LBM
+    case = synth.gaussian_cell(r=r, h_min=h_min, seed=seed)
+    if solver == "mlbm":
+        s, _ = crossval._solver(case, n_l, 3, 2, RBF_SOLVER_LBM, 15, 0.5 * h_min,
+                                dict(precision=precision, nu=1.0, g=(1.0, 0.0, 0.0), tau_plus=1.0, magic=1.0), device)
+        if unknown_rule:
+            s.lbm_set_unknown_rule(unknown_rule)
+        if tune:
+            s.autotune(20)
+    else:
+        s, v_ref = crossval._solver(case, n_l, 3, 2, RBF_SOLVER_ACM, 15, 0.0,
+                                    dict(precision=precision, nu=1.0, g=(1.0, 0.0, 0.0), v_ref=v_ref, beta=10.0),
+                                    device)
+        if tune:
+            s.autotune_persistent(200)
+    trace = []
+    t = time.perf_counter()
+    for i in range(chunks):
+        if solver == "mlbm":
+            s.step(chunk)
+        else:
+            s.solve(chunk, 1e-300, check_every=chunk)
+        k, _ = s.permeability(32)
+        F, _ = s.drag(32)
+        trace.append((chunk * (i + 1), k, F[0]))
+        if not np.isfinite(k):
+            break
+    out = dict(r=r, h_min=h_min, solver=solver, n=case.n, n_l=n_l, v_ref=v_ref, unknown_rule=unknown_rule,
+               dt=s.time_step(), trace=trace, wall_s=time.perf_counter() - t)
+    s.close()
+    return out
+
+
 def main(argv=None):
     """Command line: one study, JSON to stdout (and --out).  Under torchrun the
     porosity sweep and the seed spread spread their runs over the ranks, one GPU
@@ -200,7 +242,7 @@ def main(argv=None):
     import json
 
     ap = argparse.ArgumentParser(description=main.__doc__)
-    ap.add_argument("study", choices=("porosity", "spread", "convergence", "refinement", "stencil"))
+    ap.add_argument("study", choices=("porosity", "spread", "convergence", "refinement", "stencil", "trace"))
     ap.add_argument("--radii", default=None, help="comma-separated radii")
     ap.add_argument("--h-min", type=float, default=0.02)
     ap.add_argument("--h-list", default="0.028,0.02,0.014,0.01")
@@ -210,6 +252,12 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=4_000_000)
     ap.add_argument("--precision-acm", choices=("fp64", "fp32c"), default="fp32c")
     ap.add_argument("--solid-check-above", type=float, default=None)
+    ap.add_argument("--solver", choices=("mlbm", "mns"), default="mns", help="trace: the solver")
+    ap.add_argument("--v-ref-list", default="0.01", help="trace (MNS): comma-separated v_ref values")
+    ap.add_argument("--unknown-rules", default="0", help="trace (MLBM): comma-separated rules")
+    ap.add_argument("--n-l", type=int, default=25)
+    ap.add_argument("--chunk", type=int, default=50_000)
+    ap.add_argument("--chunks", type=int, default=4)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     radii = tuple(float(x) for x in a.radii.split(",")) if a.radii else SWEEP_RADII
@@ -226,8 +274,14 @@ def main(argv=None):
         res = [convergence_study(r, [float(x) for x in a.h_list.split(",")], **kw) for r in radii]
     elif a.study == "refinement":
         res = [refinement_parameter_study(r, a.h_min, **kw) for r in radii]
-    else:
+    elif a.study == "stencil":
         res = [stencil_size_study(r, tuple(int(x) for x in a.n_l_list.split(",")), a.h_min, **kw) for r in radii]
+    else:
+        prec = RBF_FP32C if (a.solver == "mns" and a.precision_acm == "fp32c") else RBF_FP64
+        variants = ([dict(v_ref=float(v)) for v in a.v_ref_list.split(",")] if a.solver == "mns"
+                    else [dict(unknown_rule=int(u)) for u in a.unknown_rules.split(",")])
+        res = [single_solver_trace(r, a.h_min, a.solver, a.chunk, a.chunks, n_l=a.n_l, precision=prec,
+                                   device=local, **v) for r in radii for v in variants]
     txt = json.dumps(crossval._jsonable(dict(study=a.study, args=vars(a), ranks=world,
                                              wall_s=time.perf_counter() - t, result=res)))
     if rank != 0:
