@@ -46,3 +46,40 @@ def test_gci_pairs_go_to_the_finer_grid():
 def test_refinement_error():
     assert studies.refinement_error(1.1, 1.0) == pytest.approx(0.1)
     assert studies.refinement_error(0.9, 1.0) == pytest.approx(0.1)
+
+
+def _fake_run_factory(K_of, k_of=None, fail=()):
+    def fake_run(r, h_min, seed=2, h_ratio=2.0, eps=0.295, n_l=25, **kw):
+        key = (h_min, h_ratio, eps, n_l)
+        conv = key not in fail
+        K = K_of(*key) if conv else float("nan")
+        k = (k_of or K_of)(*key) if conv else float("nan")
+        return dict(r=r, h_min=h_min, h_ratio=h_ratio, eps=eps, n_l=n_l,
+                    mlbm=dict(k=k, K=K, converged=conv), mns=dict(k=2 * k, K=2 * K, converged=conv))
+    return fake_run
+
+
+def test_refinement_study_errors_against_the_uniform_cell(monkeypatch):
+    # K = 10 on the uniform cell (ratio 1), 10 (1 + 0.01 ratio eps) otherwise; (4, 0.1) diverges
+    K_of = lambda h, ratio, eps, n_l: 10.0 if ratio == 1.0 else 10.0 * (1.0 + 0.01 * ratio * eps)
+    monkeypatch.setattr(studies, "_run", _fake_run_factory(K_of, fail={(0.02, 4.0, 0.1, 25)}))
+    out = studies.refinement_parameter_study(0.5, 0.02)
+    assert out["reference"]["h_ratio"] == 1.0
+    assert len(out["rows"]) == 9
+    for x in out["rows"]:
+        if (x["h_ratio"], x["eps"]) == (4.0, 0.1):
+            assert np.isnan(x["mlbm"]["E"]) and np.isnan(x["mns"]["E"])
+        else:
+            assert x["mlbm"]["E"] == pytest.approx(0.01 * x["h_ratio"] * x["eps"])
+            assert x["mns"]["E"] == pytest.approx(0.01 * x["h_ratio"] * x["eps"])
+
+
+def test_convergence_study_wires_gci(monkeypatch):
+    p = 2.0
+    K_of = lambda h, ratio, eps, n_l: 3.0 * (1.0 + 50.0 * h ** p) if h > 0.01 else 3.0
+    monkeypatch.setattr(studies, "_run", _fake_run_factory(K_of))
+    out = studies.convergence_study(0.3, [0.028, 0.02, 0.014, 0.01])
+    assert out["mlbm_K_p"] == pytest.approx(p)
+    assert out["mns_k_p"] == pytest.approx(p)
+    _, g = studies.gci([0.028, 0.02, 0.014, 0.01], [K_of(h, 2, 0.3, 25) for h in (0.028, 0.02, 0.014, 0.01)])
+    assert out["mlbm_K_gci"] == pytest.approx(g)
