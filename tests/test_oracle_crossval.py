@@ -6,6 +6,9 @@
 * The Gaussian spacing of Eq. refinement_function as generated by the node
   fill: nearest-neighbour distances follow h(x) across the cell, and the
   node count falls in the range the paper's discretisation gives.
+* The oracle's MNS and MLBM, independent discretisations of the same Stokes
+  flow, approach each other's steady k/d^2 as the nodes are refined (12 %,
+  7 %, 4 % on jittered cells of 1.5k, 3.5k and 6.8k nodes).
 """
 import numpy as np
 
@@ -76,3 +79,49 @@ def test_gaussian_refinement_spacing():
     w = np.asarray(c2["type"]) == 1
     assert np.all(oracle.sdf(c2["xyz"][w], c2["centre"], c2["radius"]) > -1e-9)
     assert np.all(oracle.sdf(c2["xyz"][~w], c2["centre"], c2["radius"]) > 0.0)
+
+
+def _oracle_pair(n_axis, acm_steps, lbm_steps):
+    """Both oracle solvers on one jittered cell (r = 0.35), each to a steady state:
+    k/d^2 of the MNS and of the MLBM (D3Q15, Lambda = 1, tau+ = 1, dx = h / 2) and
+    the relative change of each over its last window."""
+    case = synth.jittered_cell(r=0.35, n_axis=n_axis, seed=5)
+    n_l = 25
+    idx = oracle.knn(case["xyz"], case["xyz"], n_l)
+    w4 = oracle.acm_weights(case["xyz"], idx)
+    _, idxb = oracle.neumann_stencils(case, n_l)
+    wgb = oracle.neumann_weights(case, idxb)
+    dmin = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
+    dt = oracle.acm_dt(dmin, 1.0)
+    probes = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], 16, n_l)
+    # a sound speed (C = beta v_ref = 20) large enough that the pressure relaxes
+    # within the run; the steady state does not depend on it
+    f = np.zeros((case.n, 4))
+    ka = []
+    for _ in range(2):
+        f, _ = oracle.acm_run(case, idx, w4, idxb, wgb, f, acm_steps // 2, dt=dt, v_ref=2.0)
+        ka.append(oracle.permeability(probes, f[:, 0], 1.0, 1.0)[0])
+    dx = 0.5 / n_axis
+    u = oracle.lbm_units(1.0, 1.0, dx, (1.0, 0.0, 0.0))
+    wk = oracle.lbm_weights(case["xyz"], idx, 15, dx)
+    fl = oracle.lbm_equilibrium(15, np.ones(case.n), np.zeros((case.n, 3)))
+    kl = []
+    for _ in range(2):
+        fl = oracle.lbm_run(fl, 15, case, idx, wk, 1.0, oracle.tau_minus(1.0, 1.0), u["g_lb"], lbm_steps // 2)
+        kl.append(oracle.permeability(probes, oracle.lbm_macro(fl, 15)[:, 0] * u["vel"], 1.0, 1.0)[0])
+    return ka[-1], kl[-1], abs(ka[1] - ka[0]) / ka[1], abs(kl[1] - kl[0]) / kl[1]
+
+
+def test_oracle_solvers_agree_under_refinement():
+    """The oracle's two solvers are independent discretisations of the same Stokes
+    flow: on the same nodes their steady k/d^2 must approach each other as the
+    nodes are refined (the cross-validation of the pointwise comparison section,
+    on the CPU).  A dropped term or a wrong unit conversion in either would
+    leave a gap that does not shrink."""
+    gaps = []
+    for n_axis, acm_steps, lbm_steps in ((12, 6000, 3000), (16, 10000, 4000), (20, 20000, 6000)):
+        ka, kl, da, dl = _oracle_pair(n_axis, acm_steps, lbm_steps)
+        assert da < 2e-3 and dl < 2e-3, (n_axis, da, dl)  # both at their steady state
+        gaps.append(abs(kl - ka) / ka)
+    assert gaps[0] > gaps[1] > gaps[2], gaps
+    assert gaps[2] < 0.06, gaps
