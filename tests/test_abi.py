@@ -45,3 +45,18 @@ def test_no_gpu_fails_loudly():
     rbf._build.build()
     with pytest.raises(rbf.RbfError):
         rbf.Solver(0)
+
+
+@pytest.mark.parametrize("compiler,std,ext", [("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")])
+def test_header_compiles_for_c_and_cpp_callers(tmp_path, compiler, std, ext):
+    """The boundary is plain C: the header alone compiles as C99 and C++11 with
+    warnings as errors (no CUDA or torch types leak into it)."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not found")
+    src = tmp_path / f"use.{ext}"
+    src.write_text('#include "rbfgb.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
