@@ -8,8 +8,9 @@
   node count falls in the range the paper's discretisation gives.
 * The oracle's MNS and MLBM, independent discretisations of the same Stokes
   flow, approach each other's steady k/d^2 as the nodes are refined (12 %,
-  7 %, 4 % on jittered cells of 1.5k, 3.5k and 6.8k nodes), and the flux
-  through the five probe planes becomes equal (mass conservation).
+  7 %, 4 % on jittered cells of 1.5k, 3.5k and 6.8k nodes); the flux
+  through the five probe planes becomes equal (mass conservation) and the force
+  on the grain approaches the body force on the fluid (momentum balance).
 """
 import numpy as np
 
@@ -90,7 +91,7 @@ def _oracle_pair(n_axis, acm_steps, lbm_steps):
     n_l = 25
     idx = oracle.knn(case["xyz"], case["xyz"], n_l)
     w4 = oracle.acm_weights(case["xyz"], idx)
-    _, idxb = oracle.neumann_stencils(case, n_l)
+    wl, idxb = oracle.neumann_stencils(case, n_l)
     wgb = oracle.neumann_weights(case, idxb)
     dmin = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
     dt = oracle.acm_dt(dmin, 1.0)
@@ -117,8 +118,16 @@ def _oracle_pair(n_axis, acm_steps, lbm_steps):
         per = vals.reshape(5, -1).mean(1)
         return (per.max() - per.min()) / per.mean()
 
-    spreads = (plane_spread(f[:, 0]), plane_spread(oracle.lbm_macro(fl, 15)[:, 0]))
-    return ka[-1], kl[-1], abs(ka[1] - ka[0]) / ka[1], abs(kl[1] - kl[0]) / kl[1], spreads
+    mac = oracle.lbm_macro(fl, 15)
+    spreads = (plane_spread(f[:, 0]), plane_spread(mac[:, 0]))
+    # force on the grain over the body force on the fluid, rho |g| phi d^3
+    uvwp = np.zeros((case.n, 4))
+    uvwp[:, :3] = mac[:, :3] * u["vel"]
+    uvwp[:, 3] = (mac[:, 3] - mac[:, 3].mean()) / 3.0 * u["press"]
+    phi = oracle.porosity(case["radius"])
+    wg = w4[wl][:, :3]
+    balance = (oracle.drag(case, idx, wg, f, 1.0)[0] / phi, oracle.drag(case, idx, wg, uvwp, 1.0)[0] / phi)
+    return ka[-1], kl[-1], abs(ka[1] - ka[0]) / ka[1], abs(kl[1] - kl[0]) / kl[1], spreads, balance
 
 
 def test_oracle_solvers_agree_under_refinement():
@@ -127,12 +136,13 @@ def test_oracle_solvers_agree_under_refinement():
     nodes are refined (the cross-validation of the pointwise comparison section,
     on the CPU).  A dropped term or a wrong unit conversion in either would
     leave a gap that does not shrink."""
-    gaps, spreads = [], []
+    gaps, spreads, balance = [], [], []
     for n_axis, acm_steps, lbm_steps in ((12, 6000, 3000), (16, 10000, 4000), (20, 20000, 6000)):
-        ka, kl, da, dl, sp = _oracle_pair(n_axis, acm_steps, lbm_steps)
+        ka, kl, da, dl, sp, bal = _oracle_pair(n_axis, acm_steps, lbm_steps)
         assert da < 2e-3 and dl < 2e-3, (n_axis, da, dl)  # both at their steady state
         gaps.append(abs(kl - ka) / ka)
         spreads.append(sp)
+        balance.append(bal)
     assert gaps[0] > gaps[1] > gaps[2], gaps
     assert gaps[2] < 0.06, gaps
     # mass conservation: at steady state the same flux crosses every plane; the
@@ -141,3 +151,10 @@ def test_oracle_solvers_agree_under_refinement():
     for s in (0, 1):
         assert spreads[0][s] > spreads[1][s] > spreads[2][s], spreads
     assert spreads[2][0] < 0.02 and spreads[2][1] < 0.01, spreads
+    # force balance F_x = rho |g| phi d^3 at steady state, approached under
+    # refinement (MNS 0.72 / 0.77 / 0.85, MLBM 0.94 / 0.96 / 0.99): the wall
+    # stress quadrature, with the MNS wall gradients the coarser of the two
+    for s in (0, 1):
+        err = [abs(b[s] - 1.0) for b in balance]
+        assert err[0] > err[1] > err[2], balance
+    assert abs(balance[2][1] - 1.0) < 0.03 and abs(balance[2][0] - 1.0) < 0.2, balance
