@@ -16,7 +16,7 @@ import time
 
 import numpy as np
 
-from . import (RBF_FP64, RBF_SOLVER_ACM, RBF_SOLVER_LBM, Solver, pointwise_difference)
+from . import (RBF_EDIVERGED, RBF_FP64, RBF_SOLVER_ACM, RBF_SOLVER_LBM, RbfError, Solver, pointwise_difference)
 
 # isocontour levels of delta drawn in the paper's pointwise comparison figure
 ISO_LEVELS = {0.062: (0.1, 0.05, 0.01), 0.6526: (1.0, 0.25, 0.05)}
@@ -42,10 +42,17 @@ def run_to_steady(s: Solver, tol: float = 1e-2, window_steps: int = 10_000, max_
     converged = False
     while steps < max_steps:
         n = int(min(window_steps, max_steps - steps))
-        if s.solver == RBF_SOLVER_ACM:
-            s.solve(n, 1e-300, check_every=n, m_p=m_p)
-        else:
-            s.step(n)
+        try:
+            if s.solver == RBF_SOLVER_ACM:
+                s.solve(n, 1e-300, check_every=n, m_p=m_p)
+            else:
+                s.step(n)
+        except RbfError as e:  # the persistent driver reports non-finite fields itself
+            if e.code != RBF_EDIVERGED:
+                raise
+            steps += n
+            hist.append((steps, float("nan")))
+            break
         steps += n
         k, _ = s.permeability(m_p)
         hist.append((steps, k))
@@ -144,9 +151,22 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
     t0 = time.perf_counter()
     lbm, _ = _solver(case, n_l_lbm or n_l, k, m, RBF_SOLVER_LBM, q, dx,
                      dict(precision=precision_lbm, nu=nu, g=g, tau_plus=tau_plus, magic=magic), device)
-    acm, v_ref_used = _solver(case, n_l, k, m, RBF_SOLVER_ACM, q, 0.0,
-                              dict(precision=precision_acm, nu=nu, g=g, v_ref=v_ref, beta=beta), device)
-    setup_s = time.perf_counter() - t0
+    try:
+        acm, v_ref_used = _solver(case, n_l, k, m, RBF_SOLVER_ACM, q, 0.0,
+                                  dict(precision=precision_acm, nu=nu, g=g, v_ref=v_ref, beta=beta), device)
+    except Exception:
+        lbm.close()
+        raise
+    try:
+        return _compare(case, lbm, acm, v_ref_used, time.perf_counter() - t0, dx, unknown_rule, tune, tol,
+                        window_steps, window_steps_lbm, max_steps, m_p, keep_fields)
+    finally:
+        lbm.close()
+        acm.close()
+
+
+def _compare(case, lbm, acm, v_ref_used, setup_s, dx, unknown_rule, tune, tol, window_steps, window_steps_lbm,
+             max_steps, m_p, keep_fields):
     out = dict(n=case.n, n_wall=int((np.asarray(case["type"]) == 1).sum()), dx=dx, setup_s=setup_s)
     for name, s, w in (("mlbm", lbm, window_steps_lbm or window_steps), ("mns", acm, window_steps)):
         if name == "mlbm" and unknown_rule:
@@ -173,8 +193,6 @@ def cross_validate(case, n_l: int = 25, k: int = 3, m: int = 2, q: int = 15, dx:
     out["K_rel_diff"] = abs(out["mlbm"]["K"] - out["mns"]["K"]) / abs(out["mns"]["K"])
     if keep_fields:
         out.update(delta=delta, dv=dv, fields_mlbm=fa, fields_mns=fb)
-    lbm.close()
-    acm.close()
     return out
 
 

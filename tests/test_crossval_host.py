@@ -89,3 +89,22 @@ def test_seed_spread_aggregation(monkeypatch):
     assert out["mlbm_k_spread"] == pytest.approx(np.std([1.0, 1.1, 0.9], ddof=1) / 1.0)
     assert out["mlbm_K_spread"] == pytest.approx(out["mlbm_k_spread"])
     assert out["mns_k_n"] == 3  # the NaN run is dropped even though flagged converged
+
+
+def test_diverged_persistent_solve_ends_the_run():
+    from paper_2404_14195_gb300 import RBF_EDIVERGED, RBF_EINVAL, RbfError
+
+    class Diverging(FakeSolver):
+        def solve(self, n, tol, check_every=100, m_p=32):
+            if self.steps >= 2000:
+                raise RbfError(self.code, "non-finite fields")
+            return super().solve(n, tol, check_every, m_p)
+
+    s = Diverging(lambda t: 0.01 * (1.0 + t), 1e-5, solver=RBF_SOLVER_ACM)
+    s.code = RBF_EDIVERGED
+    r = crossval.run_to_steady(s, tol=1e-3, window_steps=1000, max_steps=10 ** 6)
+    assert not r["converged"] and r["steps"] == 3000 and math.isnan(r["history"][-1][1])
+    s = Diverging(lambda t: 0.01 * (1.0 + t), 1e-5, solver=RBF_SOLVER_ACM)
+    s.code = RBF_EINVAL  # any other error is not swallowed
+    with pytest.raises(RbfError):
+        crossval.run_to_steady(s, tol=1e-3, window_steps=1000, max_steps=10 ** 6)
