@@ -83,3 +83,40 @@ def test_convergence_study_wires_gci(monkeypatch):
     assert out["mns_k_p"] == pytest.approx(p)
     _, g = studies.gci([0.028, 0.02, 0.014, 0.01], [K_of(h, 2, 0.3, 25) for h in (0.028, 0.02, 0.014, 0.01)])
     assert out["mlbm_K_gci"] == pytest.approx(g)
+
+
+def test_cli_dispatch_and_json(monkeypatch, capsys, tmp_path):
+    """The studies command line hands its arguments to the study and prints one
+    JSON object (NaN as null); single process, no GPU."""
+    import json
+    seen = {}
+
+    def fake_sweep(radii, h_min, solid_check_above=None, _ranks=(), **kw):
+        seen.update(radii=radii, h_min=h_min, solid=solid_check_above, kw=kw)
+        return [dict(r=r, k=float("nan")) for r in radii]
+    monkeypatch.setattr(studies, "porosity_sweep", fake_sweep)
+    out = tmp_path / "o.json"
+    studies.main(["porosity", "--radii", "0.3,0.6", "--h-min", "0.03", "--solid-check-above", "0.5",
+                  "--window", "500", "--out", str(out)])
+    d = json.loads(capsys.readouterr().out)
+    assert seen["radii"] == (0.3, 0.6) and seen["h_min"] == 0.03 and seen["solid"] == 0.5
+    assert seen["kw"]["window_steps"] == 500 and seen["kw"]["device"] == 0
+    assert d["study"] == "porosity" and d["ranks"] == 1 and d["result"][0] == {"r": 0.3, "k": None}
+    assert json.loads(out.read_text()) == d
+
+
+def test_crossval_cli_dispatch(monkeypatch, capsys):
+    import json
+    from paper_2404_14195_gb300 import crossval
+    seen = {}
+
+    def fake_cv(case, **kw):
+        seen.update(kw, n=case.n, r=case["radius"])
+        return dict(mlbm=dict(history=[(1, 0.1)] * 8), mns=dict(history=[(1, 0.1)] * 8),
+                    line=dict(x=np.arange(200.0), node=np.arange(200), speed_a=np.ones(200)))
+    monkeypatch.setattr(crossval, "cross_validate", fake_cv)
+    crossval.main(["--r", "0.6526", "--h-min", "0.04", "--v-ref", "auto", "--unknown-rule", "1", "--q", "19"])
+    d = json.loads(capsys.readouterr().out)
+    assert seen["v_ref"] == "auto" and seen["unknown_rule"] == 1 and seen["q"] == 19 and seen["r"] == 0.6526
+    assert len(d["mlbm"]["history"]) == 5          # the last windows only
+    assert len(d["line"]["x"]) <= 67 and "node" not in d["line"]
