@@ -158,3 +158,27 @@ def test_oracle_solvers_agree_under_refinement():
         err = [abs(b[s] - 1.0) for b in balance]
         assert err[0] > err[1] > err[2], balance
     assert abs(balance[2][1] - 1.0) < 0.03 and abs(balance[2][0] - 1.0) < 0.2, balance
+
+
+def test_acm_steady_state_does_not_depend_on_the_sound_speed():
+    """The artificial sound speed C = beta max(max|v|, v_ref) sets how fast the
+    MNS pressure relaxes, not where it ends: run long enough, two values of
+    v_ref reach the same steady k/d^2, while after a short run the smaller one
+    is still far off (the slow transient that the cross-validation avoids with a
+    larger v_ref)."""
+    case = synth.jittered_cell(r=0.35, n_axis=12, seed=5)
+    n_l = 25
+    idx = oracle.knn(case["xyz"], case["xyz"], n_l)
+    w4 = oracle.acm_weights(case["xyz"], idx)
+    _, idxb = oracle.neumann_stencils(case, n_l)
+    wgb = oracle.neumann_weights(case, idxb)
+    dmin = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
+    dt = oracle.acm_dt(dmin, 1.0)
+    probes = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], 16, n_l)
+
+    def k_after(v_ref, steps):
+        f, _ = oracle.acm_run(case, idx, w4, idxb, wgb, np.zeros((case.n, 4)), steps, dt=dt, v_ref=v_ref)
+        return oracle.permeability(probes, f[:, 0], 1.0, 1.0)[0]
+    k_fast = k_after(2.0, 8000)
+    assert abs(k_after(0.5, 10000) - k_fast) < 1e-3 * k_fast
+    assert abs(k_after(0.01, 2000) - k_fast) > 0.3 * k_fast
