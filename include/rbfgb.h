@@ -139,7 +139,10 @@ int rbf_step(rbf_ctx *ctx, int nsteps);
 
 /* Fields in physical units, caller's node order: uvwp (n x 4) = (u, v, w, p).
  * LBM: v = (dx/dt) v_lb of the last pre-collision state, p = rho_ref (dx/dt)^2
- * (rho_lb - <rho_lb>) c_s^2. */
+ * c_s^2 (rho_lb - <rho_lb>) / <rho_lb>, <rho_lb> the node mean: the meshless
+ * streaming does not conserve mass, and at the steady state the whole density
+ * field keeps growing in proportion while v stays put, so the pressure is
+ * taken relative to the current mean density (rbf_drag uses the same p). */
 int rbf_get_fields(rbf_ctx *ctx, double *uvwp);
 /* Set the ACM state (u, v, w, p) (a warm start or a restart); C of Eq. MNS_C is
  * recomputed from the new velocity.  LBM contexts: RBF_EINVAL. */
@@ -172,14 +175,16 @@ int rbf_lbm_get_unknown_mask(rbf_ctx *ctx, uint32_t *mask);
 /* Permeability, Eq. k_definition: probes on an m_p x m_p midpoint grid on each of
  * the planes x = 0, .2, .4, .6, .8; fluid probes interpolate v_x from their own
  * n_l nearest nodes (L = 1 weights centred at the probe), solid probes count as
- * zero; q = probe mean; k/d^2 = q nu / |g|.  FP64 accumulation.  Needs
- * rbf_set_sphere.  The probe set is built on the first call and when m_p changes. */
+ * zero; q = probe mean; k/d^2 = q nu / |g|.  FP64 accumulation (compensated FP32:
+ * of hi + lo).  Needs rbf_set_sphere.  The probe set is built on the first call
+ * and when m_p changes; a rebuild that fails keeps the previous probe set
+ * (and its m_p) unchanged. */
 int rbf_permeability(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q);
 
 /* Hydrodynamic force on the grain, Eqs. stress_tensor_force and
  * integration_force, F = (A / N_b) sum_b sigma . n over wall nodes, and the drag
  * coefficient K = F_x / (6 pi r phi q mu) of Eq. K_definition with q from
- * rbf_permeability(m_p).  FP64 accumulation. */
+ * rbf_permeability(m_p).  FP64 accumulation (compensated FP32: of hi + lo). */
 int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K);
 
 /* Pointwise velocity difference of two solutions on the same nodes (the
@@ -290,6 +295,17 @@ int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep)
  * the order of the stencil sums (rounding only). */
 int rbf_set_persistent_block(rbf_ctx *ctx, int code);
 
+/* Wall-clock limit of one wait at a grid barrier of the persistent ACM driver
+ * (rbf_solve, rbf_batch_solve with this context as the first cell): a block that
+ * waits longer for the others raises the launch's error flag, every block leaves
+ * its step loop at its next barrier, and the call returns RBF_ETIMEOUT; the
+ * fields are then those of an unfinished step (call rbf_init or rbf_set_fields
+ * before the next solve).  The paper has no counterpart; this is the driver's
+ * failure detection.  Default 2 s; 1e-9 <= seconds <= 60, else RBF_EINVAL.  The
+ * cluster schedules (codes -8, -16) synchronise with the hardware cluster barrier
+ * and do not use it. */
+int rbf_set_wait_limit(rbf_ctx *ctx, double seconds);
+
 /* Number of kernel launches issued by this context since creation. */
 int64_t rbf_launch_count(const rbf_ctx *ctx);
 
@@ -396,16 +412,18 @@ int rbf_mlp_set_fused(rbf_mlp *mlp, int fused);
  * synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has no
  * counterpart; this is a deployment variant of the probe reduction.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *  - Its scratch (block partials and the sum) is one static device array of
- *    4097 doubles that every GPU loading the library holds until exit; the
- *    probe set must already exist: call rbf_permeability(ctx, m_p, ...) once
+ *  - Its scratch (4096 block partials and their sum) is one static device array
+ *    of 4097 doubles (32,776 bytes) that every GPU loading the library holds
+ *    until exit.  rbf_create looks up the array's device address (with the
+ *    context's device current) and the context keeps it, so the address is
+ *    valid for the context's whole life; this call looks nothing up.
+ *  - The probe set must already exist: call rbf_permeability(ctx, m_p, ...) once
  *    first (it builds the probes, which allocates), else RBF_EINVAL.
  *  - At most 1,048,576 fluid probes; more returns RBF_EINVAL.
- *  - The first call on a device looks up the scratch address for that device;
- *    make that first call before any stream capture.
  *  - All calls share the one array, so calls that overlap on the GPU (other
  *    contexts or streams on the same device) race; serialise them.  Each call
  *    overwrites the partials it uses, so nothing needs clearing.
+ *  - Compensated FP32 (RBF_FP32C) reads hi + lo, like rbf_permeability.
  *  - Writes *k_over_d2 and *q (either may be NULL) before returning. */
 int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q);
 

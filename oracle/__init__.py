@@ -360,6 +360,23 @@ def lbm_unknown_solid(case, q: int, dx: float) -> np.ndarray:
     return mask
 
 
+def lbm_fields(f, q: int, units):
+    """Physical (u, v, w, p) (n, 4) of a pre-collision state f (q, n): velocity of
+    Eq. macro_var times dx/dt, and p = rho_ref (dx/dt)^2 c_s^2 (rho - <rho>) /
+    <rho> with c_s^2 = 1/3, rho_ref = 1 and <rho> the node mean (Eq.
+    conversion_factors with the lattice reference density taken as the current
+    mean density: the meshless streaming does not conserve mass, so <rho> drifts
+    at the steady state while v does not; f and c f give the same fields).
+    units: lbm_units(...)."""
+    mac = lbm_macro(f, q)
+    rho = mac[:, 3]
+    mean = rho.mean()
+    out = np.empty((mac.shape[0], 4))
+    out[:, :3] = mac[:, :3] * units["vel"]
+    out[:, 3] = (rho - mean) / mean / 3.0 * units["press"]
+    return out
+
+
 def lbm_macro(f, q: int):
     """(n, 4) = (vx, vy, vz, rho) per Eq. macro_var."""
     f = _f64(f)
@@ -444,13 +461,20 @@ def drag(case, idx, wgrad_wall, uvwp, nu: float, rho: float = 1.0, area: float =
     integration_force: sigma = -p I + rho nu (grad v + grad v^T) at wall nodes,
     F_i = (A / N_b) sum_b sigma_ij n_j.  wgrad_wall (N_b, 3, n_l) are the d/dx,
     d/dy, d/dz weights of the wall nodes (in the order of np.nonzero(type)).
-    area: A (defaults to the sphere's wall area in the cell)."""
+    area: A (defaults to the sphere's wall area in the cell).
+
+    The pressure enters relative to its mean over the wall nodes.  The exact
+    surface integral of a constant pressure over the closed grain surface is
+    zero, and the pressure of the incompressible problem is fixed only up to a
+    constant; the equal-weight sum over scattered wall nodes does not annul a
+    constant (sum_b n_b != 0), so without the shift the force would follow the
+    pressure's arbitrary level (in the MNS that level drifts at steady state)."""
     wall = np.nonzero(np.asarray(case["type"]) == 1)[0]
     nb = len(wall)
     if nb == 0:
         return np.zeros(3)
     grad = np.stack([apply(idx[wall], wgrad_wall, uvwp[:, c]) for c in range(3)], 1)  # (nb, comp i, d/dx_j)
-    p = uvwp[wall, 3]
+    p = uvwp[wall, 3] - uvwp[wall, 3].mean()
     n = np.asarray(case["normal"])[wall]
     sig = -p[:, None, None] * np.eye(3)[None] + rho * nu * (grad + grad.transpose(0, 2, 1))
     f = np.einsum("bij,bj->i", sig, n)

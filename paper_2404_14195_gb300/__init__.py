@@ -106,6 +106,7 @@ ABI = {
     "rbf_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
     "rbf_autotune_persistent": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
     "rbf_set_persistent_block": (_I, [_P, _I]),
+    "rbf_set_wait_limit": (_I, [_P, _D]),
     "rbf_batch_autotune": (_I, [_P, _I, ctypes.POINTER(rbf_tune_report)]),
     "rbf_batch_create": (_I, [ctypes.POINTER(_P), _I, _P]),
     "rbf_batch_destroy": (_I, [_P]),
@@ -344,6 +345,11 @@ class Solver:
         256) + 1000 x lanes per node (2, 4, 8; 0 for one), or -8 / -16 for one
         cluster of 8 / 16 CTAs."""
         self._ck(self._L.rbf_set_persistent_block(self._h, int(code)))
+
+    def set_wait_limit(self, seconds: float):
+        """Wall-clock limit of one grid-barrier wait of the persistent ACM driver
+        (default 2 s); a wait that runs out ends the solve with RBF_ETIMEOUT."""
+        self._ck(self._L.rbf_set_wait_limit(self._h, float(seconds)))
 
     def autotune_persistent(self, trial_steps: int = 200):
         """ACM: time the persistent driver's block sizes on this case and keep the

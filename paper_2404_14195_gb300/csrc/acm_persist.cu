@@ -12,9 +12,10 @@
 // that of the multi-launch kernels in acm.cu (same operations, same order).
 //
 // The grid barrier is a counter plus a generation word; waiting blocks give up
-// after a wall-clock limit, raise an error flag and leave the loop, so a launch
-// whose blocks are not co-resident ends with RBF_ETIMEOUT instead of hanging.
-// The cooperative launch itself guarantees co-residency.
+// after a wall-clock limit (PersistCtl::wait_ns, 2 s by default), raise an error
+// flag and leave the loop, so a launch whose blocks are not co-resident ends with
+// RBF_ETIMEOUT instead of hanging.  Every wait also ends as soon as another block
+// has raised the flag.  The cooperative launch itself guarantees co-residency.
 //
 // CP = true is the compensated FP32 state of acm.cu (hi + lo pairs, comp_add
 // updates, gathers of the hi words); its residual differences include the low
@@ -29,10 +30,9 @@ namespace rbf {
 
 namespace {
 
-constexpr uint64_t BARRIER_NS = 2000000000ull;
-
-// returns false (and raises *err) if the other blocks did not arrive in time
-__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int32_t *err) {
+// returns false (and raises *err) if the other blocks did not arrive within
+// wait_ns nanoseconds, or if another block has raised *err
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int32_t *err, uint64_t wait_ns) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -48,7 +48,7 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, i
             const uint64_t t0 = tc::globaltimer_ns();
             while (*vgen == g) {
                 if (*(volatile int32_t *)err) { ok = 0; break; }
-                if (tc::globaltimer_ns() - t0 > BARRIER_NS) {
+                if (tc::globaltimer_ns() - t0 > wait_ns) {
                     atomicExch(err, 2);
                     ok = 0;
                     break;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
             cluster_barrier();
             return true;
         } else {
-            return rbf::grid_barrier(count, gen, nb, err);
+            return rbf::grid_barrier(count, gen, nb, err, ctl.wait_ns);
         }
     };
     for (int64_t step = 0; step < ctl.max_steps; ++step) {
@@ -363,10 +363,13 @@ __global__ void __launch_bounds__(256) k_acm_persistent(const CellDesc<T> *__res
                         d2 += ctl.partial[(int64_t)b * 2 * PERSIST_MAX_CELLS + 2 * c];
                         v2 += ctl.partial[(int64_t)b * 2 * PERSIST_MAX_CELLS + 2 * c + 1];
                     }
-                    const double res = v2 > 0.0 ? sqrt(d2) / sqrt(v2) : 0.0;
+                    // a non-finite value anywhere in the cell's velocity makes d2 or v2
+                    // non-finite (a NaN fails every comparison, so test before dividing)
+                    const bool bad = !isfinite(d2) || !isfinite(v2);
+                    const double res = bad ? (double)NAN : (v2 > 0.0 ? sqrt(d2) / sqrt(v2) : 0.0);
                     ctl.resid[c] = res;
                     ctl.steps[c] = step + 1;
-                    if (!isfinite(res)) ctl.done[c] = 3;
+                    if (bad) ctl.done[c] = 3;
                     else if (v2 > 0.0 && res < ctl.tol) ctl.done[c] = 1;
                 }
             }

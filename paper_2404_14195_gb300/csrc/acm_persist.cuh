@@ -44,6 +44,7 @@ struct PersistCtl {
     int check_every;
     double tol;
     int n_p;
+    uint64_t wait_ns;        // wall-clock limit of one grid-barrier wait (nanoseconds)
 };
 
 // cp selects the compensated kernel (every cell then carries low words); block:

@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -52,9 +51,12 @@ struct DeviceGuard {
 
 // FP32 storage (plain or compensated)
 bool is_f32(const rbf_ctx *c) { return c->prec != RBF_FP64; }
+// low words of ACM field c (0..3: u, v, w, p) of a compensated FP32 state, else null
+const float *low_words(const rbf_ctx *c, int f) { return c->prec == RBF_FP32C ? c->l32[f].p : nullptr; }
 
 int persistent_solve(std::vector<rbf_ctx *> &cs, const rbf_solve_opts *o, std::vector<int64_t> &steps,
                      std::vector<double> &resid, std::vector<int32_t> &done, std::string &err);
+cudaError_t static_flux_lookup(double **out);
 
 void drop_graph(rbf_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -262,7 +264,8 @@ int rbf_create(rbf_ctx **out, int device, void *cuda_stream) {
         ctx->own_stream = true;
     }
     if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
-        ctx->vmax.alloc(2) != cudaSuccess || ctx->scal.alloc(16) != cudaSuccess || ctx->status.alloc(4) != cudaSuccess) {
+        ctx->vmax.alloc(2) != cudaSuccess || ctx->scal.alloc(16) != cudaSuccess || ctx->status.alloc(4) != cudaSuccess ||
+        static_flux_lookup(&ctx->static_flux) != cudaSuccess) {
         rbf_destroy(ctx);
         return RBF_ECUDA;
     }
@@ -674,7 +677,7 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
     CK(ctx->mac.alloc(4 * n));
     CK(ctx->stage.alloc((size_t)std::max(4, ctx->q) * n));
     {
-        const size_t need = (size_t)(4 * (std::max<int64_t>(n, 5LL * 512 * 512) / 256 + 8));
+        const size_t need = (size_t)(8 * (std::max<int64_t>(n, 5LL * 512 * 512) / 256 + 8));
         if (ctx->partial.n < need) CK(ctx->partial.alloc(need));
     }
     CK(cudaStreamSynchronize(ctx->st));
@@ -914,6 +917,14 @@ int rbf_set_persistent_block(rbf_ctx *ctx, int code) {
     return RBF_OK;
 }
 
+int rbf_set_wait_limit(rbf_ctx *ctx, double seconds) {
+    if (!ctx) return RBF_EINVAL;
+    if (!(seconds >= 1e-9 && seconds <= 60.0)) return fail(ctx, RBF_EINVAL, "rbf_set_wait_limit: 1e-9 <= seconds <= 60");
+    ctx->wait_ns = (uint64_t)std::llround(seconds * 1e9);
+    if (ctx->wait_ns < 1) ctx->wait_ns = 1;
+    return RBF_OK;
+}
+
 int rbf_autotune_persistent(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     if (!ctx) return RBF_EINVAL;
     if (!ctx->inited || ctx->solver != RBF_SOLVER_ACM)
@@ -1033,12 +1044,15 @@ int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f) {
 }
 
 namespace {
+// Probe set of Eq. k_definition for m_p: built into local arrays and committed
+// to the context (points, stencils, weights, fluid count, m_p) only once every
+// step has succeeded, so a failed rebuild leaves the previous probe set whole.
 int ensure_probes(rbf_ctx *ctx, int m_p) {
     if (ctx->m_p == m_p && ctx->pidx.p) return RBF_OK;
     const int64_t tot = 5LL * m_p * m_p;
     const int n_l = ctx->n_l;
-    DevArr<double> pts;
-    DevArr<int32_t> flag, scan, tmp;
+    DevArr<double> pts, pxyz, pw;
+    DevArr<int32_t> flag, scan, tmp, pidx;
     CK(pts.alloc(3 * tot)); CK(flag.alloc(tot + 1)); CK(scan.alloc(tot + 1)); CK(tmp.alloc(scan_tmp_len(tot + 1)));
     CK(flag.zero(ctx->st));
     k_probe_points<<<nblk(tot), 256, 0, ctx->st>>>(m_p, ctx->c[0], ctx->c[1], ctx->c[2], ctx->r, ctx->has_sphere, pts.p, flag.p);
@@ -1046,28 +1060,31 @@ int ensure_probes(rbf_ctx *ctx, int m_p) {
     int32_t nfl = 0;
     CK(cudaMemcpyAsync(&nfl, scan.p + tot, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    ctx->np_fluid = nfl;
-    CK(ctx->pxyz.alloc(3 * std::max<int64_t>(nfl, 1)));
-    k_probe_compact<<<nblk(tot), 256, 0, ctx->st>>>(tot, pts.p, flag.p, scan.p, ctx->pxyz.p);
+    CK(pxyz.alloc(3 * std::max<int64_t>(nfl, 1)));
+    k_probe_compact<<<nblk(tot), 256, 0, ctx->st>>>(tot, pts.p, flag.p, scan.p, pxyz.p);
     ctx->launches += 2;
-    CK(ctx->pidx.alloc(std::max<int64_t>(nfl, 1) * n_l));
-    CK(ctx->pw.alloc(std::max<int64_t>(nfl, 1) * n_l));
+    CK(pidx.alloc(std::max<int64_t>(nfl, 1) * n_l));
+    CK(pw.alloc(std::max<int64_t>(nfl, 1) * n_l));
     CK(ctx->status.zero(ctx->st));
     if (nfl > 0) {
-        CK(launch_knn(nfl, ctx->pxyz.p, nullptr, ctx->xyz.p, ctx->perm.p, ctx->type.p, 0, ctx->G, ctx->cstart.p,
-                      ctx->citems.p, n_l, ctx->pidx.p, n_l, 0, ctx->status.p, ctx->st));
+        CK(launch_knn(nfl, pxyz.p, nullptr, ctx->xyz.p, ctx->perm.p, ctx->type.p, 0, ctx->G, ctx->cstart.p,
+                      ctx->citems.p, n_l, pidx.p, n_l, 0, ctx->status.p, ctx->st));
         OpSpec op{OP_INTERP, {0.0, 0.0, 0.0}};
         DevArr<OpSpec> d_op;
         CK(d_op.alloc(1));
         CK(cudaMemcpyAsync(d_op.p, &op, sizeof(OpSpec), cudaMemcpyHostToDevice, ctx->st));
-        CK(launch_weights(nfl, ctx->xyz.p, ctx->pxyz.p, nullptr, 0, n_l, ctx->pidx.p, ctx->phs_k, ctx->mono_m, 1,
-                          d_op.p, 1, ctx->pw.p, nullptr, ctx->status.p + 1, ctx->st));
+        CK(launch_weights(nfl, ctx->xyz.p, pxyz.p, nullptr, 0, n_l, pidx.p, ctx->phs_k, ctx->mono_m, 1,
+                          d_op.p, 1, pw.p, nullptr, ctx->status.p + 1, ctx->st));
         ctx->launches += 2;
     }
     int32_t st2[2] = {0, 0};
     CK(cudaMemcpyAsync(st2, ctx->status.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     if (st2[0] || st2[1]) return fail(ctx, RBF_ESINGULAR, "probe stencils failed");
+    ctx->pxyz.swap(pxyz);
+    ctx->pidx.swap(pidx);
+    ctx->pw.swap(pw);
+    ctx->np_fluid = nfl;
     ctx->m_p = m_p;
     return RBF_OK;
 }
@@ -1077,13 +1094,13 @@ int probe_q(rbf_ctx *ctx, int m_p, double *qout) {
     int rc = ensure_probes(ctx, m_p);
     if (rc) return rc;
     if (ctx->solver == RBF_SOLVER_ACM) {
-        if (is_f32(ctx)) CK(launch_probe_sum<float>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
-        else CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        if (is_f32(ctx)) CK(launch_probe_sum<float>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, low_words(ctx, 0), 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        else CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, nullptr, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 2;
     } else {
         if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
         else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, ctx->partial.p, ctx->scal.p + 4, ctx->st));
+        CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, nullptr, 4, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 3;
     }
     double s = 0.0;
@@ -1118,7 +1135,8 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
     const double mu = ctx->rho * ctx->prm.nu;
     if (ctx->solver == RBF_SOLVER_ACM) {
         if (is_f32(ctx)) {
-            FieldView<float> f{ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, 1, 1.0, 0.0, 1.0};
+            FieldView<float> f{ctx->a32[0].p, ctx->a32[1].p, ctx->a32[2].p, ctx->a32[3].p, 1, 1.0, 0.0, 1.0,
+                               low_words(ctx, 0), low_words(ctx, 1), low_words(ctx, 2), low_words(ctx, 3)};
             CK(launch_drag<float>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
         } else {
             FieldView<double> f{ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, 1, 1.0, 0.0, 1.0};
@@ -1133,16 +1151,19 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
         CK(cudaMemcpyAsync(sums, ctx->scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
         const double vel = ctx->dx / ctx->lbm_dt;
+        const double dmean = sums[3] / (double)ctx->n;  // <rho> - 1
         FieldView<double> f{ctx->mac.p, ctx->mac.p + 1, ctx->mac.p + 2, ctx->mac.p + 3, 4, vel,
-                            sums[3] / (double)ctx->n, ctx->rho * vel * vel / 3.0};
+                            dmean, ctx->rho * vel * vel / (3.0 * (1.0 + dmean))};
         CK(launch_drag<double>(ctx->nb, ctx->n_l, ctx->wall.p, ctx->idx.p, ctx->wgw64.p, ctx->nrm.p, f, mu, ctx->partial.p, ctx->scal.p + 8, ctx->st));
         ctx->launches += 5;
     }
-    double Fs[3];
-    CK(cudaMemcpyAsync(Fs, ctx->scal.p + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    double Fs[7];
+    CK(cudaMemcpyAsync(Fs, ctx->scal.p + 8, 7 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    // wall quadrature with the wall-mean pressure removed: sum (sigma + pbar I) . n
     const double A = wall_area_of(ctx->r);
-    for (int a = 0; a < 3; ++a) F[a] = ctx->nb ? A / (double)ctx->nb * Fs[a] : 0.0;
+    const double pbar = ctx->nb ? Fs[3] / (double)ctx->nb : 0.0;
+    for (int a = 0; a < 3; ++a) F[a] = ctx->nb ? A / (double)ctx->nb * (Fs[a] + pbar * Fs[4 + a]) : 0.0;
     if (K) {
         double qq = 0.0;
         int rc = probe_q(ctx, m_p > 0 ? m_p : 32, &qq);
@@ -1271,6 +1292,7 @@ int persistent_solve_T(std::vector<rbf_ctx *> &cs, cudaStream_t st, const rbf_so
     ctl.resid = d_res.p; ctl.partial = d_part.p; ctl.ncells = nc; ctl.nslices = (int64_t)sl.size();
     ctl.nwslices = (int64_t)wsl.size(); ctl.slices = d_sl.p; ctl.wslices = d_wsl.p; ctl.max_steps = o->max_steps;
     ctl.check_every = o->check_every > 0 ? o->check_every : 100; ctl.tol = o->tol; ctl.n_p = cs[0]->n_p;
+    ctl.wait_ns = cs[0]->wait_ns;
     CK(cudaEventRecord(ctx->ev0, st));
     if (csize) CK(acm_launch_persistent_cluster<T>(d_desc.p, ctl, csize, cp, st));
     else CK(acm_launch_persistent<T>(d_desc.p, ctl, nblocks, block, group, cp, st));
@@ -1381,39 +1403,30 @@ int rbf_solve(rbf_ctx *ctx, const rbf_solve_opts *opts, rbf_solve_result *res) {
 // allocated.  rbf_permeability_static runs a copy of the same probe reduction
 // whose partials and result live in the file-scope array below instead, so the
 // call itself allocates no device memory.  Host code cannot use the array's name
-// as a device address (it names a host-side stand-in), so its address is looked
-// up with cudaGetSymbolAddress once per device, with that device current, the
-// first time the entry point runs on it.
+// as a device address (it names a host-side stand-in), so rbf_create looks the
+// address up with cudaGetSymbolAddress, with the context's device current, and
+// keeps it in the context (static_flux_lookup); a context cannot outlive its
+// device's reset, so the address stays valid for the context's whole life.
 #define RBF_STATIC_FLUX_BLOCKS 4096  // up to 4096 * 256 = 1,048,576 fluid probes
-static __device__ __align__(256) double g_static_flux[RBF_STATIC_FLUX_BLOCKS + 32];
-static double *g_static_flux_addr[64] = {nullptr};
-static std::mutex g_static_flux_mu;
+// [0, RBF_STATIC_FLUX_BLOCKS): block partials; [RBF_STATIC_FLUX_BLOCKS]: their sum
+static __device__ __align__(256) double g_static_flux[RBF_STATIC_FLUX_BLOCKS + 1];
 
 namespace {
 
-cudaError_t static_flux_scratch(int device, double **out) {
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_static_flux_mu);
-    if (!g_static_flux_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_flux);  // the device is current (DeviceGuard)
-        if (e != cudaSuccess) return e;
-        g_static_flux_addr[device] = (double *)p;
-    }
-    *out = g_static_flux_addr[device];
-    return cudaSuccess;
-}
-
 // block b writes its partial to scratch[b]; every launch overwrites the partials of
-// the blocks it runs, so nothing has to start at zero
+// the blocks it runs, so nothing has to start at zero.  vxl: the low words of a
+// compensated FP32 vx (summed as hi + lo in FP64), or null.
 template <typename T>
 __global__ void __launch_bounds__(256) k_probe_sum_static(int64_t np, int n_l, const int32_t *idx, const double *w,
-                                                          const T *vx, int64_t stride, double *scratch) {
+                                                          const T *vx, const T *vxl, int64_t stride, double *scratch) {
     __shared__ double red[8];
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double s = 0.0;
     if (p < np)
-        for (int j = 0; j < n_l; ++j) s += w[p * n_l + j] * (double)vx[idx[p * n_l + j] * stride];
+        for (int j = 0; j < n_l; ++j) {
+            const int64_t q = idx[p * n_l + j] * stride;
+            s += w[p * n_l + j] * (vxl ? (double)vx[q] + (double)vxl[q] : (double)vx[q]);
+        }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -1432,6 +1445,14 @@ __global__ void k_static_final(double *scratch, int64_t nb) {
     if (threadIdx.x == 0) scratch[RBF_STATIC_FLUX_BLOCKS] = s;
 }
 
+// the device address of g_static_flux on the current device
+cudaError_t static_flux_lookup(double **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_flux);
+    *out = (double *)p;
+    return e;
+}
+
 }  // namespace
 
 extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2, double *q) {
@@ -1443,20 +1464,20 @@ extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2,
     if (nb > RBF_STATIC_FLUX_BLOCKS)
         return fail(ctx, RBF_EINVAL, "rbf_permeability_static: more than 1,048,576 fluid probes (static scratch limit)");
     DeviceGuard dg(ctx->device);
-    double *scratch = nullptr;
-    CK(static_flux_scratch(ctx->device, &scratch));
+    double *scratch = ctx->static_flux;
+    if (!scratch) return fail(ctx, RBF_ECUDA, "rbf_permeability_static: no scratch address (rbf_create failed to look it up)");
     double s = 0.0;
     if (nb > 0) {
         if (ctx->solver == RBF_SOLVER_ACM) {
             if (is_f32(ctx))
-                k_probe_sum_static<float><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, 1, scratch);
+                k_probe_sum_static<float><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a32[0].p, low_words(ctx, 0), 1, scratch);
             else
-                k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, 1, scratch);
+                k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, nullptr, 1, scratch);
         } else {
             if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
             else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
             ++ctx->launches;
-            k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, 4, scratch);
+            k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, nullptr, 4, scratch);
         }
         k_static_final<<<1, 32, 0, ctx->st>>>(scratch, nb);
         ctx->launches += 2;

@@ -33,6 +33,10 @@ struct DevArr {
         return e;
     }
     cudaError_t zero(cudaStream_t st) { return n ? cudaMemsetAsync(p, 0, n * sizeof(T), st) : cudaSuccess; }
+    void swap(DevArr &o) {
+        T *tp = p; p = o.p; o.p = tp;
+        size_t tn = n; n = o.n; o.n = tn;
+    }
 };
 
 }  // namespace rbf
@@ -82,6 +86,7 @@ struct rbf_ctx {
     int64_t np_fluid = 0;
     DevArr<double> pxyz, pw;
     DevArr<int32_t> pidx;
+    double *static_flux = nullptr;  // device address of rbf_permeability_static's file-scope scratch
     // scratch
     DevArr<double> partial, scal, mac, stage;  // stage: host <-> device field transfers
     DevArr<int32_t> status;
@@ -95,6 +100,7 @@ struct rbf_ctx {
     int persist_cluster = 0;          // > 0: run it as one cluster of that many CTAs (8 or 16)
     int persist_group = 1;            // lanes per node of its sweeps (1, 2, 4, 8)
     double persist_ms = 0.0;          // device time of its last launch
+    uint64_t wait_ns = 2000000000ull; // wall-clock limit of one grid-barrier wait of that driver
     int gblock = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;

@@ -70,71 +70,85 @@ cudaError_t launch_residual(int64_t n, const uint8_t *type, const T *u, const T 
     return final_sum(partial, nb, 2, out2, st);
 }
 
-// probe interpolation: out_sum = sum_p sum_j w_pj vx[S_p(j)] * scale
+// probe interpolation: out_sum = sum_p sum_j w_pj vx[S_p(j)]  (vx + vxl for a
+// compensated state)
 template <typename T>
 __global__ void __launch_bounds__(256) k_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w,
-                                                   const T *vx, int64_t stride, double *partial) {
+                                                   const T *vx, const T *vxl, int64_t stride, double *partial) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double acc[1] = {0.0};
     if (p < np) {
         double s = 0.0;
-        for (int j = 0; j < n_l; ++j) s += w[p * n_l + j] * (double)vx[idx[p * n_l + j] * stride];
+        for (int j = 0; j < n_l; ++j) {
+            const int64_t q = idx[p * n_l + j] * stride;
+            const double v = vxl ? (double)vx[q] + (double)vxl[q] : (double)vx[q];
+            s += w[p * n_l + j] * v;
+        }
         acc[0] = s;
     }
     block_partial<1>(acc, partial);
 }
 
 template <typename T>
-cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, int64_t stride,
-                             double *partial, double *out, cudaStream_t st) {
+cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, const T *vxl,
+                             int64_t stride, double *partial, double *out, cudaStream_t st) {
     if (np == 0) return cudaMemsetAsync(out, 0, sizeof(double), st);
     int64_t nb = (np + 255) / 256;
-    k_probe_sum<T><<<(unsigned)nb, 256, 0, st>>>(np, n_l, idx, w, vx, stride, partial);
+    k_probe_sum<T><<<(unsigned)nb, 256, 0, st>>>(np, n_l, idx, w, vx, vxl, stride, partial);
     return final_sum(partial, nb, 1, out, st);
 }
 
 // sigma . n at wall nodes: sigma_ij = -p d_ij + rho nu (d_j v_i + d_i v_j).
 // Velocity components and pressure are read through (pointer, stride) views and
-// scaled to physical units: v = vs * vel, p = (praw - p0) * ps.
+// scaled to physical units: v = vs * vel, p = (praw - p0) * ps.  Per wall node the
+// kernel adds (sigma . n, p, n): the host turns the sums into the force with the
+// wall-mean pressure removed, F = sum sigma . n + pbar sum n, so that a constant
+// pressure contributes nothing (the exact surface integral of a constant is zero;
+// the equal-weight quadrature over scattered wall nodes is not).
 template <typename T>
 __global__ void __launch_bounds__(256) k_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx,
                                               const double *wg, const double *nrm, FieldView<T> f, double mu,
                                               double *partial) {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (b < nb) {
         int64_t i = wall[b];
         double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // G[comp][dir] = d v_comp / d x_dir
         const double *gx = wg + b * 3 * n_l, *gy = gx + n_l, *gz = gy + n_l;
         for (int j = 0; j < n_l; ++j) {
-            int64_t q = idx[i * n_l + j];
-            double vq[3] = {(double)f.u[q * f.stride] * f.vel, (double)f.v[q * f.stride] * f.vel,
-                            (double)f.w[q * f.stride] * f.vel};
+            const int64_t q = idx[i * n_l + j] * f.stride;
+            double vq[3] = {(double)f.u[q], (double)f.v[q], (double)f.w[q]};
+            if (f.ul) { vq[0] += (double)f.ul[q]; vq[1] += (double)f.vl[q]; vq[2] += (double)f.wl[q]; }
+            vq[0] *= f.vel; vq[1] *= f.vel; vq[2] *= f.vel;
             for (int c = 0; c < 3; ++c) {
                 G[c][0] += gx[j] * vq[c];
                 G[c][1] += gy[j] * vq[c];
                 G[c][2] += gz[j] * vq[c];
             }
         }
-        double p = ((double)f.p[i * f.stride] - f.p0) * f.ps;
+        double praw = (double)f.p[i * f.stride];
+        if (f.pl) praw += (double)f.pl[i * f.stride];
+        double p = (praw - f.p0) * f.ps;
         double n3[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
         for (int a = 0; a < 3; ++a) {
             double s = -p * n3[a];
             for (int c = 0; c < 3; ++c) s += mu * (G[a][c] + G[c][a]) * n3[c];
             acc[a] = s;
         }
+        acc[3] = p;
+        acc[4] = n3[0]; acc[5] = n3[1]; acc[6] = n3[2];
     }
-    block_partial<3>(acc, partial);
+    block_partial<7>(acc, partial);
 }
 
 template <typename T>
 cudaError_t launch_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx, const double *wg,
-                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out3,
+                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out7,
                         cudaStream_t st) {
-    if (nb == 0) return cudaMemsetAsync(out3, 0, 3 * sizeof(double), st);
+    if (nb == 0) return cudaMemsetAsync(out7, 0, 7 * sizeof(double), st);
     int64_t nbl = (nb + 255) / 256;
     k_drag<T><<<(unsigned)nbl, 256, 0, st>>>(nb, n_l, wall, idx, wg, nrm, f, mu, partial);
-    return final_sum(partial, nbl, 3, out3, st);
+    return final_sum(partial, nbl, 7, out7, st);
 }
 
 __global__ void k_min(const double *in, int64_t n, double *partial) {
@@ -290,7 +304,9 @@ cudaError_t launch_pointwise(int64_t n, const double *va, const double *vb, doub
     return cudaGetLastError();
 }
 
-// LBM macro buffer (sorted, lattice units, (vx, vy, vz, drho)) -> physical uvwp, caller order
+// LBM macro buffer (sorted, lattice units, (vx, vy, vz, rho - 1)) -> physical uvwp,
+// caller order; p = ps c_s^2 (rho - <rho>) / <rho> (pressure relative to the mean
+// density, in units of it)
 __global__ void k_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
                              const double *drho_sum, double *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -300,7 +316,7 @@ __global__ void k_lbm_fields(int64_t n, const int32_t *perm, const double *mac, 
     out[4 * o] = mac[4 * i] * vel;
     out[4 * o + 1] = mac[4 * i + 1] * vel;
     out[4 * o + 2] = mac[4 * i + 2] * vel;
-    out[4 * o + 3] = (mac[4 * i + 3] - mean) * (1.0 / 3.0) * ps;
+    out[4 * o + 3] = (mac[4 * i + 3] - mean) / (1.0 + mean) * (1.0 / 3.0) * ps;
 }
 cudaError_t launch_lbm_fields(int64_t n, const int32_t *perm, const double *mac, double vel, double ps,
                               const double *drho_sum, double *out, cudaStream_t st) {
@@ -358,8 +374,8 @@ cudaError_t launch_export_weights(int64_t n, int n_l, int n_ops, int op, const i
 #define RBF_RED_INST(T)                                                                                         \
     template cudaError_t launch_residual<T>(int64_t, const uint8_t *, const T *, const T *, const T *, const T *, \
                                             const T *, const T *, double *, double *, cudaStream_t);            \
-    template cudaError_t launch_probe_sum<T>(int64_t, int, const int32_t *, const double *, const T *, int64_t,  \
-                                             double *, double *, cudaStream_t);                                 \
+    template cudaError_t launch_probe_sum<T>(int64_t, int, const int32_t *, const double *, const T *, const T *, \
+                                             int64_t, double *, double *, cudaStream_t);                        \
     template cudaError_t launch_drag<T>(int64_t, int, const int32_t *, const int32_t *, const double *,          \
                                         const double *, const FieldView<T> &, double, double *, double *,       \
                                         cudaStream_t);                                                          \

@@ -6,23 +6,28 @@ namespace rbf {
 
 // Read-only view of a velocity / pressure field: component pointers with a
 // common element stride, scaled to physical units v = raw * vel,
-// p = (raw - p0) * ps.
+// p = (raw - p0) * ps.  ul .. pl: the low words of a compensated FP32 state
+// (raw = hi + lo, summed in FP64), null otherwise.
 template <typename T>
 struct FieldView {
     const T *u, *v, *w, *p;
     int64_t stride;
     double vel, p0, ps;
+    const T *ul = nullptr, *vl = nullptr, *wl = nullptr, *pl = nullptr;
 };
 
 template <typename T>
 cudaError_t launch_residual(int64_t n, const uint8_t *type, const T *u, const T *v, const T *w, const T *uo,
                             const T *vo, const T *wo, double *partial, double *out2, cudaStream_t st);
+// vxl: low words of a compensated FP32 vx (value = hi + lo in FP64), or null
 template <typename T>
-cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, int64_t stride,
-                             double *partial, double *out, cudaStream_t st);
+cudaError_t launch_probe_sum(int64_t np, int n_l, const int32_t *idx, const double *w, const T *vx, const T *vxl,
+                             int64_t stride, double *partial, double *out, cudaStream_t st);
+// out7 = (sum_b sigma . n [3], sum_b p_b, sum_b n_b [3]) over the wall nodes;
+// partial needs 7 doubles per 256 wall nodes
 template <typename T>
 cudaError_t launch_drag(int64_t nb, int n_l, const int32_t *wall, const int32_t *idx, const double *wg,
-                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out3,
+                        const double *nrm, const FieldView<T> &f, double mu, double *partial, double *out7,
                         cudaStream_t st);
 template <typename T>
 cudaError_t launch_acm_export(int64_t n, const int32_t *perm, const T *u, const T *v, const T *w, const T *p,

@@ -11,6 +11,12 @@ import numpy as np
 from . import RBF_FP32C, Batch, Mlp, Solver
 
 N_L_DEFAULT = 25
+# Reference speed of Eq. MNS_C for the steady solves here: C = beta v_ref = 20
+# makes the artificial sound waves relax faster than the viscous modes on cells
+# of this family (h ~ 1/12 .. 1/20), so a start's remaining error decays at the
+# viscous rate and a better start saves steps; with v_ref = 0.01 the slow
+# artificial-compressibility mode sets the time to steady whatever the start.
+V_REF_DEFAULT = 2.0
 
 
 def signed_distance(xyz, centre, r):
@@ -20,7 +26,7 @@ def signed_distance(xyz, centre, r):
 
 
 def steady_training_set(cases, n_l=N_L_DEFAULT, tol=1e-6, max_steps=2_000_000, check_every=1000,
-                        precision=RBF_FP32C, device=0):
+                        precision=RBF_FP32C, device=0, v_ref=V_REF_DEFAULT):
     """Solve every case to steady state in one batched persistent launch; returns
     (xyz, radius, sdf, targets (u, v, w, p)) over all nodes, the per-cell results
     and the wall time."""
@@ -29,7 +35,7 @@ def steady_training_set(cases, n_l=N_L_DEFAULT, tol=1e-6, max_steps=2_000_000, c
     for c in cases:
         b.add_cell(c, n_l)
     b.build(3, 2)
-    b.init(precision=precision, v_ref=0.01)
+    b.init(precision=precision, v_ref=v_ref)
     res = b.solve(max_steps, tol, check_every=check_every)
     X, R, S, T = [], [], [], []
     for i, c in enumerate(cases):
@@ -71,16 +77,53 @@ def train(data, init_params, steps=3000, batch=1024, lr=2e-3, seed=7, device=0, 
 
 
 def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32C, tol=1e-6, max_steps=2_000_000,
-               check_every=1000, m_p=24, device=0):
+               check_every=1000, m_p=24, device=0, v_ref=V_REF_DEFAULT):
     """Steady solve of one case from a zero start or from the network's prediction."""
     s = Solver(device)
     s.set_case(case)
     s.build_stencils(n_l)
     s.compute_weights(solver=0)
-    s.init(precision=precision, v_ref=0.01)
+    s.init(precision=precision, v_ref=v_ref)
     t0 = time.perf_counter()
     if mlp is not None:
         mlp.warm_start(s, 1.0)
     r = s.solve(max_steps, tol, check_every=check_every, m_p=m_p)
     r["seconds"] = time.perf_counter() - t0
     return s, r
+
+
+def permeability_history(case, mlp=None, chunk=200, max_steps=20000, n_l=N_L_DEFAULT, precision=RBF_FP32C,
+                         m_p=24, device=0, v_ref=V_REF_DEFAULT):
+    """k/d^2 after every `chunk` steps of one case from a zero start or from the
+    network's prediction: [(steps, k/d^2, seconds since the start)], step 0 the
+    start itself (the network's evaluation and the warm start included in the
+    time, the permeability reads excluded)."""
+    s = Solver(device)
+    s.set_case(case)
+    s.build_stencils(n_l)
+    s.compute_weights(solver=0)
+    s.init(precision=precision, v_ref=v_ref)
+    t0 = time.perf_counter()
+    if mlp is not None:
+        mlp.warm_start(s, 1.0)
+    t_run = time.perf_counter() - t0
+    hist = [(0, s.permeability(m_p)[0], t_run)]
+    steps = 0
+    while steps < max_steps:
+        t1 = time.perf_counter()
+        s.solve(chunk, 1e-300, check_every=chunk, m_p=m_p)
+        t_run += time.perf_counter() - t1
+        steps += chunk
+        hist.append((steps, s.permeability(m_p)[0], t_run))
+    s.close()
+    return hist
+
+
+def first_within(hist, k_ref, rel=1e-4):
+    """The first (steps, k, seconds) of a permeability history after which k stays
+    within rel of k_ref until the end of the history; None if it never settles."""
+    ok = [abs(k - k_ref) <= rel * abs(k_ref) for _, k, _ in hist]
+    for i in range(len(ok)):
+        if all(ok[i:]):
+            return hist[i]
+    return None

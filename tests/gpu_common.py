@@ -43,3 +43,17 @@ def oracle_acm_setup(case, n_l, k=3, m=2):
     wgb = oracle.neumann_weights(case, idxb, k, m)
     dmin = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
     return dict(idx=idx, w4=w4, wl=wl, idxb=idxb, wgb=wgb, h_min=dmin)
+
+
+def bf16_forward(theta, X):
+    """The warm-start network's output (n, 4) with the GPU kernels' rounding points:
+    BF16 inputs, weights and hidden activations, wide accumulation, FP32 bias
+    (the FP64 layers of oracle/mlp.py with BF16 rounding inserted)."""
+    from oracle import mlp as om
+    L = om.unpack(theta)
+    h = om.bf16_round(X)
+    for li, (W, b) in enumerate(L):
+        z = h @ om.bf16_round(W).T + b
+        if li < 4:
+            h = om.bf16_round(om.gelu(z))
+    return z[:, :4]

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gpu_common import bf16_forward as _bf16_forward
 from gpu_common import gpu_or_skip
 from oracle import mlp as om
 
@@ -37,16 +38,6 @@ def _data(n, seed=0):
     T = np.stack([np.sin(2 * np.pi * xyz[:, 0]) * r, np.cos(2 * np.pi * xyz[:, 1]) * sdf,
                   0.3 * np.sin(2 * np.pi * (xyz[:, 0] + xyz[:, 2])), r * sdf], 1)
     return xyz, r, sdf, X, T
-
-
-def _bf16_forward(theta, X):
-    L = om.unpack(theta)
-    h = om.bf16_round(X)
-    for li, (W, b) in enumerate(L):
-        z = h @ om.bf16_round(W).T + b
-        if li < 4:
-            h = om.bf16_round(om.gelu(z))
-    return z[:, :4]
 
 
 def test_forward_matches_bf16_model(rbf):

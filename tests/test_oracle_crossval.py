@@ -121,9 +121,7 @@ def _oracle_pair(n_axis, acm_steps, lbm_steps):
     mac = oracle.lbm_macro(fl, 15)
     spreads = (plane_spread(f[:, 0]), plane_spread(mac[:, 0]))
     # force on the grain over the body force on the fluid, rho |g| phi d^3
-    uvwp = np.zeros((case.n, 4))
-    uvwp[:, :3] = mac[:, :3] * u["vel"]
-    uvwp[:, 3] = (mac[:, 3] - mac[:, 3].mean()) / 3.0 * u["press"]
+    uvwp = oracle.lbm_fields(fl, 15, u)
     phi = oracle.porosity(case["radius"])
     wg = w4[wl][:, :3]
     balance = (oracle.drag(case, idx, wg, f, 1.0)[0] / phi, oracle.drag(case, idx, wg, uvwp, 1.0)[0] / phi)

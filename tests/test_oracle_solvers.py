@@ -2,7 +2,9 @@
 
 ACM (MNS section): the analytic plane Poiseuille flow is a fixed point of the
 discrete scheme to rounding (quadratic profile, m = 2 exact), a zero start
-converges to it, and its wall shear balances the body force exactly.
+converges to it, and its wall shear balances the body force exactly; the wall
+Neumann update reproduces a manufactured radial pressure whose normal
+derivative vanishes on the sphere, and not one whose normal derivative does not.
 LBM (MLBM section): velocity-set moments, equilibrium moments, collision
 invariants and relaxation rates of the TRT kernel, the lattice-shift limit of
 the meshless streaming step, uniform forcing on a periodic lattice.
@@ -230,3 +232,119 @@ def test_stream_rows_equals_full_stream():
     rows = np.concatenate([np.nonzero(case["type"] == 1)[0][:20], np.arange(0, case.n, 13)])
     part = oracle.lbm_stream_rows(fpost, q, case, rows, idx[rows], wk[rows])
     assert np.array_equal(part, full[:, rows])
+
+
+def _neumann_step(n_axis, seed, f):
+    """One MNS step with v = 0, g = 0 and one pressure iteration from p = f(|x - c|):
+    the fluid pressure cannot change (the divergence of v' = 0 vanishes) and the
+    wall nodes take the Neumann update of the MNS boundary conditions."""
+    from gpu_common import oracle_acm_setup
+    case = synth.jittered_cell(r=0.35, n_axis=n_axis, seed=seed)
+    o = oracle_acm_setup(case, 25)
+    s = np.linalg.norm(oracle.min_image(case["xyz"] - case["centre"]), axis=1)
+    wall = case["type"] == 1
+    uvwp = np.zeros((case.n, 4))
+    uvwp[:, 3] = f(s)
+    uvwp[wall, 3] = 7.0  # any value: the update overwrites it
+    out, _ = oracle.acm_run(case, o["idx"], o["w4"], o["idxb"], o["wgb"], uvwp, 1, g=(0.0, 0.0, 0.0), dt=1e-4, n_p=1)
+    assert np.array_equal(out[~wall, 3], f(s)[~wall])
+    return out[wall, 3]
+
+
+def test_neumann_wall_pressure_reproduces_a_field_with_zero_normal_derivative():
+    """MNS boundary conditions (dp/dn = 0 at the wall; the fluid-only Neumann
+    stencil of the build's reading): p = 1 + 20 (|x - c| - r)^2 has zero normal
+    derivative on the sphere, so every wall node must come out at p = 1 up to the
+    one-sided stencil's truncation error, which shrinks faster than h under
+    refinement.  A flipped sign gives ~-1, dropping the Neumann solve for a copy
+    of the nearest fluid node errs by 0.18 / 0.09 on these cells."""
+    f = lambda s: 1.0 + 20.0 * (s - 0.35) ** 2  # noqa: E731
+    e14 = np.abs(_neumann_step(14, 5, f) - 1.0).max()
+    e20 = np.abs(_neumann_step(20, 1, f) - 1.0).max()
+    assert e14 <= 0.05 and e20 <= 0.02, (e14, e20)
+    assert e20 <= 0.5 * e14  # h ratio 1.43: better than first order
+
+
+def test_neumann_wall_pressure_does_not_reproduce_a_sloped_field():
+    """The same update imposes dp/dn = 0, not an interpolation: for
+    p = 1 + (|x - c| - r), whose normal derivative is 1 at the wall, the wall
+    values miss p = 1 by a first-order amount (an interpolating update would
+    reproduce this linear-in-distance field closely)."""
+    f = lambda s: 1.0 + (s - 0.35)  # noqa: E731
+    for n_axis, seed in ((14, 5), (20, 1)):
+        assert (_neumann_step(n_axis, seed, f) - 1.0).mean() > 0.02
+
+
+def test_mns_steady_drag_ignores_the_drifting_pressure_level():
+    """At the MNS steady state on scattered nodes the velocity stops changing, but
+    the RBF-FD divergence is not conservative (its node sum does not vanish), so
+    the pressure iteration of Eq. MNS_pressure adds the same amount to every
+    fluid pressure each step: the level drifts linearly while grad p stays put.
+    The drag (Eqs. stress_tensor_force, integration_force) must not follow it:
+    over 4,000 further steps the pressure level moves by O(1) and F_x by less than
+    1e-10 relative; a constant added to p changes F not at all."""
+    from gpu_common import oracle_acm_setup
+    case = synth.jittered_cell(r=0.35, n_axis=10, seed=5)
+    o = oracle_acm_setup(case, 25)
+    dt = oracle.acm_dt(o["h_min"], 1.0)
+    wl = o["wl"]
+    f, res = oracle.acm_run(case, o["idx"], o["w4"], o["idxb"], o["wgb"], np.zeros((case.n, 4)), 10000, dt=dt,
+                            v_ref=5.0)
+    assert res[-1] < 1e-14
+    f2, res2 = oracle.acm_run(case, o["idx"], o["w4"], o["idxb"], o["wgb"], f, 4000, dt=dt, v_ref=5.0)
+    fluid = case["type"] == 0
+    assert np.abs(f2[:, :3] - f[:, :3]).max() <= 1e-12 * np.abs(f[:, :3]).max()
+    dp = f2[fluid, 3] - f[fluid, 3]
+    assert abs(dp.mean()) > 0.5 and dp.std() < 1e-9 * abs(dp.mean())  # a uniform drift
+    F1 = oracle.drag(case, o["idx"], o["w4"][wl][:, :3], f, 1.0)
+    F2 = oracle.drag(case, o["idx"], o["w4"][wl][:, :3], f2, 1.0)
+    assert abs(F2[0] - F1[0]) <= 1e-10 * abs(F1[0])
+    g = f.copy()
+    g[:, 3] += 123.0
+    assert np.abs(oracle.drag(case, o["idx"], o["w4"][wl][:, :3], g, 1.0) - F1).max() <= 1e-12 * abs(F1[0])
+
+
+def test_lbm_fields_of_an_equilibrium_and_scale_invariance():
+    """lbm_fields on f = f_eq(rho_i, v_i) (Eq. feq) returns v_i dx/dt and
+    c_s^2 (rho_i / <rho> - 1) (dx/dt)^2, and the same fields for 3 f: the MLBM
+    flow does not depend on the overall mass level."""
+    rng = np.random.default_rng(3)
+    n, q = 500, 19
+    rho = 1.0 + 0.01 * rng.standard_normal(n)
+    vel = 0.01 * rng.standard_normal((n, 3))
+    u = oracle.lbm_units(1.0, 0.8, 0.01, (1.0, 0.0, 0.0))
+    f = oracle.lbm_equilibrium(q, rho, vel)
+    got = oracle.lbm_fields(f, q, u)
+    assert np.abs(got[:, :3] - vel * u["vel"]).max() <= 1e-12 * u["vel"]
+    want_p = (rho / rho.mean() - 1.0) / 3.0 * u["press"]
+    assert np.abs(got[:, 3] - want_p).max() <= 1e-12 * np.abs(want_p).max()
+    assert np.abs(oracle.lbm_fields(3.0 * f, q, u) - got).max() <= 1e-12 * np.abs(got).max()
+
+
+def test_mlbm_steady_state_has_a_growing_mass_mode_that_leaves_k_and_K():
+    """The meshless streaming step (Eq. LBM_streaming) is not mass-conservative:
+    at the steady state the mean density keeps changing at a constant rate while
+    the velocity field stays put.  k/d^2 and K, computed from lbm_fields, are
+    steady to 1e-9 over 4,000 further steps although <rho> moves by ~1e-5."""
+    from gpu_common import oracle_acm_setup
+    case = synth.jittered_cell(r=0.35, n_axis=10, seed=5)
+    o = oracle_acm_setup(case, 25)
+    idx, q = o["idx"], 19
+    dx = o["h_min"] / 2.0
+    u = oracle.lbm_units(1.0, 0.8, dx, (1.0, 0.0, 0.0))
+    wk = oracle.lbm_weights(case["xyz"], idx, q, dx)
+    tm = oracle.tau_minus(0.8, 3.0 / 16.0)
+    pr = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], 16, 25)
+    wg = o["w4"][o["wl"]][:, :3]
+    f = oracle.lbm_run(oracle.lbm_equilibrium(q, np.ones(case.n), np.zeros((case.n, 3))), q, case, idx, wk, 0.8, tm,
+                       u["g_lb"], 14000)
+    out = []
+    for _ in range(2):
+        fld = oracle.lbm_fields(f, q, u)
+        k, qq = oracle.permeability(pr, fld[:, 0], 1.0, 1.0)
+        K = oracle.drag_coefficient(oracle.drag(case, idx, wg, fld, 1.0)[0], case["radius"], qq, 1.0)
+        out.append((k, K, oracle.lbm_macro(f, q)[:, 3].mean()))
+        f = oracle.lbm_run(f, q, case, idx, wk, 0.8, tm, u["g_lb"], 4000)
+    (k1, K1, m1), (k2, K2, m2) = out
+    assert abs(m2 - m1) > 1e-6
+    assert abs(k2 - k1) <= 1e-9 * k1 and abs(K2 - K1) <= 1e-9 * K1, (k2 / k1 - 1, K2 / K1 - 1)

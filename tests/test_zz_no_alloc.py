@@ -18,7 +18,7 @@ from gpu_common import gpu_or_skip
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("solver", ["acm", "lbm"])
+@pytest.mark.parametrize("solver", ["acm", "acm_fp32c", "lbm"])
 def test_static_permeability_matches_allocating_entry_point(solver):
     rbf = gpu_or_skip()
     case = synth.jittered_cell(r=0.3, n_axis=12, seed=21)
@@ -26,9 +26,10 @@ def test_static_permeability_matches_allocating_entry_point(solver):
     s.set_case(case)
     s.build_stencils(25)
     m_p = 20
-    if solver == "acm":
+    if solver.startswith("acm"):
         rep = s.compute_weights(solver=rbf.RBF_SOLVER_ACM)
-        s.init(precision=rbf.RBF_FP64, dt=0.1 * rep["h_min"] ** 2 / 2.0, v_ref=0.01)
+        prec = rbf.RBF_FP32C if solver == "acm_fp32c" else rbf.RBF_FP64
+        s.init(precision=prec, dt=0.1 * rep["h_min"] ** 2 / 2.0, v_ref=0.01)
         s.step(120)
     else:
         s.compute_weights(solver=rbf.RBF_SOLVER_LBM, q=19, dx=0.5 / 12)
