@@ -50,7 +50,18 @@ enum { RBF_SOLVER_ACM = 0, RBF_SOLVER_LBM = 1 };
  * explicit iteration stalls short of the steady state, the pairs keep them.
  * rbf_get_fields returns hi + lo; rbf_set_fields splits each value into the
  * pair. */
-enum { RBF_FP64 = 0, RBF_FP32 = 1, RBF_FP32C = 2 };
+/* RBF_FP32R (MLBM only): FP32 steps that converge to the FP64 fixed point.  The
+ * state is f = f_b + d with an FP64 base f_b and an FP32 correction d.  Every
+ * 64 steps a refresh folds d into f_b, takes one FP64 step of f_b and keeps its
+ * residual r = F(f_b) - f_b in FP32 (d = r); the other steps advance only the
+ * correction in FP32, d <- S(d) + r, with S the FP32 step without the body force
+ * (the force is inside r).  At the steady state r vanishes in FP64, so the
+ * result is the FP64 step's fixed point, while 63 of 64 steps move FP32 data.
+ * Plain FP32 populations round every step's state to 2^-24 of the populations'
+ * size; when the per-step forcing is a small fraction of it (the steady lattice
+ * velocity is ~10^4 steps of forcing on the paper's resolutions) those roundings
+ * add up to a bias of ~1e-4 in k/d^2.  Outputs read f_b + d in FP64. */
+enum { RBF_FP64 = 0, RBF_FP32 = 1, RBF_FP32C = 2, RBF_FP32R = 3 };
 enum { RBF_FLUID = 0, RBF_WALL = 1 };
 /* operator ids for rbf_get_weights */
 enum {
@@ -114,7 +125,7 @@ int rbf_compute_weights(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q, 
 int rbf_get_weights(rbf_ctx *ctx, int op, double *out);
 
 typedef struct {
-    int precision;   /* RBF_FP64, RBF_FP32 or RBF_FP32C (ACM): storage and arithmetic of the steps */
+    int precision;   /* RBF_FP64, RBF_FP32, RBF_FP32C (ACM) or RBF_FP32R (LBM): storage and arithmetic of the steps */
     double nu;       /* kinematic viscosity */
     double g[3];     /* body acceleration */
     double rho;      /* density (ACM) / reference density (LBM); 0 -> 1 */

@@ -25,7 +25,7 @@ from . import _build
 RBF_OK, RBF_EINVAL, RBF_ECUDA, RBF_ESINGULAR = 0, -1, -2, -3
 RBF_EDIVERGED, RBF_ENOTCONVERGED, RBF_ETIMEOUT, RBF_ENOMEM = -4, -5, -6, -7
 RBF_SOLVER_ACM, RBF_SOLVER_LBM = 0, 1
-RBF_FP64, RBF_FP32, RBF_FP32C = 0, 1, 2
+RBF_FP64, RBF_FP32, RBF_FP32C, RBF_FP32R = 0, 1, 2, 3
 RBF_OP_DX, RBF_OP_DY, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_LBM0 = 0, 1, 2, 3, 16
 
 _ERRNAMES = {RBF_EINVAL: "EINVAL", RBF_ECUDA: "ECUDA", RBF_ESINGULAR: "ESINGULAR",

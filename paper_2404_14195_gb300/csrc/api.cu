@@ -54,6 +54,34 @@ bool is_f32(const rbf_ctx *c) { return c->prec != RBF_FP64; }
 // low words of ACM field c (0..3: u, v, w, p) of a compensated FP32 state, else null
 const float *low_words(const rbf_ctx *c, int f) { return c->prec == RBF_FP32C ? c->l32[f].p : nullptr; }
 
+// stored values of one LBM population buffer (either layout, padding included)
+int64_t lbm_state_len(const rbf_ctx *c) { return (int64_t)lbm_rec_len(c->q) * c->npad; }
+// FP64 schedule of the refined FP32 mode's refresh step: one node per thread on
+// the layout of the current FP32 schedule
+int refine_schedule(const rbf_ctx *c) {
+    return c->lbm_layout == LBM_LAYOUT_NODES ? LBM_RECORD_PER_THREAD : LBM_NODE_PER_THREAD;
+}
+// The current LBM state as shifted populations in FP64 (refined FP32: base plus
+// correction, written into the FP64 scratch f64[1]), or null when it is plain FP32
+// (then read f32[cur]).
+cudaError_t lbm_state64(rbf_ctx *c, const double **out) {
+    *out = nullptr;
+    if (c->prec == RBF_FP64) { *out = c->f64[c->cur].p; return cudaSuccess; }
+    if (c->prec != RBF_FP32R) return cudaSuccess;
+    ++c->launches;
+    *out = c->f64[1].p;
+    return lbm_launch_refine_combine(lbm_state_len(c), c->f64[0].p, c->f32[c->cur].p, c->f64[1].p, c->st);
+}
+// moments of the current LBM state into c->mac (lbm_launch_macro; the caller
+// counts that launch, lbm_state64 counts its own)
+cudaError_t lbm_macro_current(rbf_ctx *c) {
+    const double *f64 = nullptr;
+    cudaError_t e = lbm_state64(c, &f64);
+    if (e != cudaSuccess) return e;
+    if (f64) return lbm_launch_macro<double>(c->n, c->npad, c->lbm_layout, c->q, f64, c->gl, c->mac.p, c->st);
+    return lbm_launch_macro<float>(c->n, c->npad, c->lbm_layout, c->q, c->f32[c->cur].p, c->gl, c->mac.p, c->st);
+}
+
 int persistent_solve(std::vector<rbf_ctx *> &cs, const rbf_solve_opts *o, std::vector<int64_t> &steps,
                      std::vector<double> &resid, std::vector<int32_t> &done, std::string &err);
 cudaError_t static_flux_lookup(double **out);
@@ -71,12 +99,25 @@ int switch_schedule(rbf_ctx *ctx, int variant) {
     if (ctx->inited && ctx->solver == RBF_SOLVER_LBM && to != ctx->lbm_layout) {
         drop_graph(ctx);
         const int c = ctx->cur;
-        if (ctx->prec == RBF_FP64)
+        if (ctx->prec == RBF_FP32R) {
+            // base + correction into the scratch, relaid out as the new base; zero
+            // correction, and a refresh at the next step
+            const double *f = nullptr;
+            CK(lbm_state64(ctx, &f));
+            CK(lbm_launch_relayout<double>(ctx->npad, ctx->q, ctx->lbm_layout, ctx->f64[1].p, to, ctx->f64[0].p, ctx->st));
+            CK(ctx->f32[0].zero(ctx->st));
+            CK(ctx->f32[1].zero(ctx->st));
+            ctx->refine_phase = 0;
+            ++ctx->launches;
+        } else if (ctx->prec == RBF_FP64) {
             CK(lbm_launch_relayout<double>(ctx->npad, ctx->q, ctx->lbm_layout, ctx->f64[c].p, to, ctx->f64[c ^ 1].p, ctx->st));
-        else
+            ++ctx->launches;
+            ctx->cur = c ^ 1;
+        } else {
             CK(lbm_launch_relayout<float>(ctx->npad, ctx->q, ctx->lbm_layout, ctx->f32[c].p, to, ctx->f32[c ^ 1].p, ctx->st));
-        ++ctx->launches;
-        ctx->cur = c ^ 1;
+            ++ctx->launches;
+            ctx->cur = c ^ 1;
+        }
     }
     ctx->lbm_layout = to;
     ctx->variant = variant;
@@ -182,11 +223,41 @@ LbmArgs<T> lbm_args(rbf_ctx *ctx, DevArr<T> *f, const DevArr<T> &ws, int cur) {
     return g;
 }
 
-// enqueue `steps` steps starting from (parity, cur); updates them
+// enqueue `steps` steps starting from (parity, cur, refined-FP32 phase); updates
+// them (phase: ctx->refine_phase when null)
 cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_t *launches,
-                          LaunchRecorder *rec = nullptr) {
+                          LaunchRecorder *rec = nullptr, int *phase = nullptr) {
     cudaError_t e = cudaSuccess;
+    int &ph = phase ? *phase : ctx->refine_phase;
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+        if (ctx->solver == RBF_SOLVER_LBM && ctx->prec == RBF_FP32R) {
+            // f = base + delta.  Refresh: fold delta into the base, one FP64 step of
+            // the base into the scratch, r = fl(F(base) - base), delta = r (so this
+            // step ends exactly at F(base)).  Other steps: delta <- S(delta) + r with
+            // S the FP32 step without the body force (its forcing is inside r).
+            const int64_t tot = lbm_state_len(ctx);
+            if (ph == 0) {
+                e = lbm_launch_refine_fold(tot, ctx->f64[0].p, ctx->f32[cur].p, ctx->st);
+                if (e == cudaSuccess)
+                    e = lbm_launch_step<double>(lbm_args<double>(ctx, ctx->f64, ctx->ws64, 0), ctx->q, ctx->st,
+                                                refine_schedule(ctx));
+                if (e == cudaSuccess)
+                    e = lbm_launch_refine_residual(tot, ctx->f64[1].p, ctx->f64[0].p, ctx->rr.p, ctx->f32[cur ^ 1].p,
+                                                   ctx->st);
+                *launches += 3;
+            } else {
+                LbmArgs<float> a = lbm_args<float>(ctx, ctx->f32, ctx->ws32, cur);
+                a.gx = a.gy = a.gz = 0.0f;
+                a.radd = ctx->rr.p;
+                if (rec) rec->begin(ctx->st, 0);
+                e = lbm_launch_step<float>(a, ctx->q, ctx->st, ctx->variant);
+                if (rec) rec->end(ctx->st);
+                ++*launches;
+            }
+            cur ^= 1;
+            ph = (ph + 1) % ctx->refine_m;
+            continue;
+        }
         if (ctx->solver == RBF_SOLVER_ACM) {
             if (is_f32(ctx)) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
             else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
@@ -204,18 +275,23 @@ cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_
 }
 
 int run_steps(rbf_ctx *ctx, int64_t nsteps) {
-    const int chunk = ctx->solver == RBF_SOLVER_ACM ? 16 : 32;  // even: parity / buffer return to start
+    // even: parity / buffer return to start; refined FP32: one refresh window, so
+    // the refresh phase returns to start as well
+    const bool refined = ctx->solver == RBF_SOLVER_LBM && ctx->prec == RBF_FP32R;
+    const int chunk = ctx->solver == RBF_SOLVER_ACM ? 16 : (refined ? ctx->refine_m : 32);
     int64_t full = nsteps / chunk, rem = nsteps % chunk;
     int64_t kl = 0;
     if (full > 0) {
+        const int ph0 = refined ? ctx->refine_phase : 0;
         if (!ctx->gexec || ctx->gparity != ctx->parity || ctx->gcur != ctx->cur || ctx->gprec != ctx->prec ||
-            ctx->gsteps != chunk || ctx->gvariant != ctx->variant || ctx->gblock != ctx->acm_block) {
+            ctx->gsteps != chunk || ctx->gvariant != ctx->variant || ctx->gblock != ctx->acm_block ||
+            ctx->gphase != ph0) {
             drop_graph(ctx);
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-            int par = ctx->parity, cu = ctx->cur;
+            int par = ctx->parity, cu = ctx->cur, ph = ph0;
             int64_t dummy = 0;
-            cudaError_t e = enqueue_steps(ctx, chunk, par, cu, &dummy);
+            cudaError_t e = enqueue_steps(ctx, chunk, par, cu, &dummy, nullptr, &ph);
             cudaError_t e2 = cudaStreamEndCapture(ctx->st, &g);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "capture");
             if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
@@ -228,6 +304,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
             ctx->gprec = ctx->prec;
             ctx->gvariant = ctx->variant;
             ctx->gblock = ctx->acm_block;
+            ctx->gphase = ph0;
             ctx->last_kernel_launches = dummy;
         }
         int64_t per_graph = ctx->last_kernel_launches;
@@ -546,21 +623,36 @@ int compute_weights_impl(rbf_ctx *ctx, int phs_k, int mono_m, int solver, int q,
     const int n_out = n_ops;
     CK(ctx->ws32.alloc(ctx->npad * n_out * n_l));
     CK(ctx->ws64.alloc(ctx->npad * n_out * n_l));
-    if (solver == RBF_SOLVER_ACM) {
-        CK(launch_pack_f32(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
-        CK(launch_pack_f64(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
-    } else {
-        CK(lbm_launch_pack_f32(n, q, n_l, ctx->w64.p, ctx->ws32.p, ctx->st));
-        CK(lbm_launch_pack_f64(n, q, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+    {
+        // the FP32 pack is made from rows rounded with their sums kept
+        DevArr<double> wr;
+        CK(wr.alloc(n * n_ops * n_l));
+        CK(launch_round_rows_f32(n * n_ops, n_l, ctx->w64.p, wr.p, ctx->st));
+        if (solver == RBF_SOLVER_ACM) {
+            CK(launch_pack_f32(n, n_ops, 0, n_out, n_l, wr.p, ctx->ws32.p, ctx->st));
+            CK(launch_pack_f64(n, n_ops, 0, n_out, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+        } else {
+            CK(lbm_launch_pack_f32(n, q, n_l, wr.p, ctx->ws32.p, ctx->st));
+            CK(lbm_launch_pack_f64(n, q, n_l, ctx->w64.p, ctx->ws64.p, ctx->st));
+        }
+        ctx->launches += 3;
+        CK(cudaStreamSynchronize(ctx->st));  // wr is freed on return
     }
-    ctx->launches += 2;
     const int64_t nbpad = (nb + 31) & ~31LL;
     if (solver == RBF_SOLVER_ACM) {
         CK(ctx->wn32.alloc(nbpad * n_l));
         CK(ctx->wn64.alloc(nbpad * n_l));
-        CK(launch_pack_normal_f32(nb, n_l, ctx->wall.p, ctx->nrm.p, ctx->wgb64.p, ctx->wn32.p, ctx->st));
+        {
+            DevArr<double> nr, nrr;
+            CK(nr.alloc(nb * n_l));
+            CK(nrr.alloc(nb * n_l));
+            CK(launch_normal_rows(nb, n_l, ctx->wall.p, ctx->nrm.p, ctx->wgb64.p, nr.p, ctx->st));
+            CK(launch_round_rows_f32(nb, n_l, nr.p, nrr.p, ctx->st));
+            CK(launch_pack_f32(nb, 1, 0, 1, n_l, nrr.p, ctx->wn32.p, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));  // nr, nrr are freed on return
+        }
         CK(launch_pack_normal_f64(nb, n_l, ctx->wall.p, ctx->nrm.p, ctx->wgb64.p, ctx->wn64.p, ctx->st));
-        ctx->launches += 2;
+        ctx->launches += 4;
         ctx->mask.release();
     } else {
         ctx->wn32.release();
@@ -620,10 +712,13 @@ int rbf_get_weights(rbf_ctx *ctx, int op, double *out) {
 int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
     if (!ctx || !p) return RBF_EINVAL;
     if (!ctx->weights_ok) return fail(ctx, RBF_EINVAL, "rbf_init: compute weights first");
-    if (p->precision != RBF_FP32 && p->precision != RBF_FP64 && p->precision != RBF_FP32C)
+    if (p->precision != RBF_FP32 && p->precision != RBF_FP64 && p->precision != RBF_FP32C &&
+        p->precision != RBF_FP32R)
         return fail(ctx, RBF_EINVAL, "rbf_init: bad precision");
     if (p->precision == RBF_FP32C && ctx->solver != RBF_SOLVER_ACM)
         return fail(ctx, RBF_EINVAL, "rbf_init: RBF_FP32C applies to the ACM solver only");
+    if (p->precision == RBF_FP32R && ctx->solver != RBF_SOLVER_LBM)
+        return fail(ctx, RBF_EINVAL, "rbf_init: RBF_FP32R applies to the LBM solver only");
     if (!(p->nu > 0.0)) return fail(ctx, RBF_EINVAL, "rbf_init: nu must be > 0");
     DeviceGuard dg(ctx->device);
     CK(cudaStreamSynchronize(ctx->st));
@@ -639,6 +734,8 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
     for (auto &a : ctx->a64) a.release();
     for (auto &a : ctx->f32) a.release();
     for (auto &a : ctx->f64) a.release();
+    ctx->rr.release();
+    ctx->refine_phase = 0;
     if (ctx->solver == RBF_SOLVER_ACM) {
         const double cfl = p->cfl > 0.0 ? p->cfl : 0.1;
         ctx->dt = p->dt > 0.0 ? p->dt : cfl * ctx->h_min * ctx->h_min / (2.0 * p->nu);
@@ -663,7 +760,14 @@ int rbf_init(rbf_ctx *ctx, const rbf_params *p) {
         ctx->cur = 0;
         ctx->lbm_layout = lbm_layout_of(ctx->variant);
         const int64_t sz = (int64_t)lbm_rec_len(ctx->q) * npad;  // room for either layout
-        if (is_f32(ctx)) {
+        if (ctx->prec == RBF_FP32R) {
+            // base = the initial state in FP64, correction and residual zero
+            CK(ctx->f64[0].alloc(sz)); CK(ctx->f64[1].alloc(sz)); CK(ctx->f64[0].zero(ctx->st));
+            LbmArgs<double> a = lbm_args<double>(ctx, ctx->f64, ctx->ws64, 1);  // writes f64[0]
+            CK(lbm_launch_init<double>(a, ctx->q, ctx->st));
+            CK(ctx->f32[0].alloc(sz)); CK(ctx->f32[1].alloc(sz)); CK(ctx->rr.alloc(sz));
+            CK(ctx->f32[0].zero(ctx->st)); CK(ctx->f32[1].zero(ctx->st)); CK(ctx->rr.zero(ctx->st));
+        } else if (is_f32(ctx)) {
             CK(ctx->f32[0].alloc(sz)); CK(ctx->f32[1].alloc(sz)); CK(ctx->f32[1].zero(ctx->st));
             LbmArgs<float> a = lbm_args<float>(ctx, ctx->f32, ctx->ws32, 1);  // writes f32[0]
             CK(lbm_launch_init<float>(a, ctx->q, ctx->st));
@@ -746,6 +850,7 @@ int save_state(rbf_ctx *ctx, StateCopy &sc) {
         CK(add(ctx->f32[i].p, ctx->f32[i].n * sizeof(float)));
         CK(add(ctx->f64[i].p, ctx->f64[i].n * sizeof(double)));
     }
+    CK(add(ctx->rr.p, ctx->rr.n * sizeof(float)));
     CK(add(ctx->vmax.p, ctx->vmax.n * sizeof(unsigned long long)));
     return RBF_OK;
 }
@@ -763,7 +868,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     if (trial_steps < 2 || trial_steps > 2000) return fail(ctx, RBF_EINVAL, "rbf_autotune: 2 <= trial_steps <= 2000");
     DeviceGuard dg(ctx->device);
     drop_graph(ctx);
-    const int par0 = ctx->parity, cur0 = ctx->cur, lay0 = ctx->lbm_layout;
+    const int par0 = ctx->parity, cur0 = ctx->cur, lay0 = ctx->lbm_layout, ph0 = ctx->refine_phase;
     StateCopy sc;
     int rc = save_state(ctx, sc);
     if (rc) return rc;
@@ -773,6 +878,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
         ctx->parity = par0;
         ctx->cur = cur0;
         ctx->lbm_layout = lay0;
+        ctx->refine_phase = ph0;
         return r;
     };
     std::vector<int> cands;
@@ -793,11 +899,11 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
             ctx->acm_block = cands[c];
         }
         int64_t kl = 0;
-        int par = ctx->parity, cu = ctx->cur;
-        cudaError_t e = enqueue_steps(ctx, 2, par, cu, &kl);  // warm-up
+        int par = ctx->parity, cu = ctx->cur, ph = ctx->refine_phase;
+        cudaError_t e = enqueue_steps(ctx, 2, par, cu, &kl, nullptr, &ph);  // warm-up
         CK(e);
         CK(cudaEventRecord(ctx->ev0, ctx->st));
-        e = enqueue_steps(ctx, trial_steps, par, cu, &kl);
+        e = enqueue_steps(ctx, trial_steps, par, cu, &kl, nullptr, &ph);
         CK(e);
         CK(cudaEventRecord(ctx->ev1, ctx->st));
         CK(cudaEventSynchronize(ctx->ev1));
@@ -984,8 +1090,7 @@ int rbf_get_fields(rbf_ctx *ctx, double *uvwp) {
         else CK(launch_acm_export<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, ctx->a64[3].p, out.p, ctx->st));
         ++ctx->launches;
     } else {
-        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(lbm_macro_current(ctx));
         CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
         const double vel = ctx->dx / ctx->lbm_dt, ps = ctx->rho * vel * vel;
         CK(launch_lbm_fields(ctx->n, ctx->perm.p, ctx->mac.p, vel, ps, ctx->scal.p + 3, out.p, ctx->st));
@@ -1022,8 +1127,10 @@ int rbf_lbm_get_populations(rbf_ctx *ctx, double *f) {
     if (!ctx->inited || ctx->solver != RBF_SOLVER_LBM) return fail(ctx, RBF_EINVAL, "rbf_lbm_get_populations: no LBM state");
     DeviceGuard dg(ctx->device);
     DevArr<double> &out = ctx->stage;
-    if (is_f32(ctx)) CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
-    else CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
+    const double *f64 = nullptr;
+    CK(lbm_state64(ctx, &f64));
+    if (f64) CK(lbm_launch_export<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, f64, ctx->perm.p, out.p, ctx->st));
+    else CK(lbm_launch_export<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, out.p, ctx->st));
     ++ctx->launches;
     CK(cudaMemcpyAsync(f, out.p, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1036,8 +1143,15 @@ int rbf_lbm_set_populations(rbf_ctx *ctx, const double *f) {
     DeviceGuard dg(ctx->device);
     DevArr<double> &in = ctx->stage;
     CK(cudaMemcpyAsync(in.p, f, (size_t)ctx->q * ctx->n * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-    if (is_f32(ctx)) CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
-    else CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    if (ctx->prec == RBF_FP32R) {  // the new state becomes the base; refresh at the next step
+        CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[0].p, ctx->perm.p, in.p, ctx->st));
+        CK(ctx->f32[ctx->cur].zero(ctx->st));
+        ctx->refine_phase = 0;
+    } else if (is_f32(ctx)) {
+        CK(lbm_launch_import<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    } else {
+        CK(lbm_launch_import<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->perm.p, in.p, ctx->st));
+    }
     ++ctx->launches;
     CK(cudaStreamSynchronize(ctx->st));
     return RBF_OK;
@@ -1098,8 +1212,7 @@ int probe_q(rbf_ctx *ctx, int m_p, double *qout) {
         else CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, nullptr, 1, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 2;
     } else {
-        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(lbm_macro_current(ctx));
         CK(launch_probe_sum<double>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, nullptr, 4, ctx->partial.p, ctx->scal.p + 4, ctx->st));
         ctx->launches += 3;
     }
@@ -1144,8 +1257,7 @@ int rbf_drag(rbf_ctx *ctx, int m_p, double F[3], double *K) {
         }
         ctx->launches += 2;
     } else {
-        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(lbm_macro_current(ctx));
         CK(launch_sum_f64(ctx->mac.p, ctx->n, 4, 4, ctx->partial.p, ctx->scal.p, ctx->st));
         double sums[4];
         CK(cudaMemcpyAsync(sums, ctx->scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
@@ -1188,8 +1300,7 @@ int velocity_to(rbf_ctx *ctx, double *out) {
             CK(launch_velocity<double>(ctx->n, ctx->perm.p, ctx->a64[0].p, ctx->a64[1].p, ctx->a64[2].p, nullptr, nullptr, nullptr, 1, 1.0, out, ctx->st));
         ++ctx->launches;
     } else {
-        if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-        else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+        CK(lbm_macro_current(ctx));
         const double *m = ctx->mac.p;
         CK(launch_velocity<double>(ctx->n, ctx->perm.p, m, m + 1, m + 2, nullptr, nullptr, nullptr, 4, ctx->dx / ctx->lbm_dt, out, ctx->st));
         ctx->launches += 2;
@@ -1474,8 +1585,7 @@ extern "C" int rbf_permeability_static(rbf_ctx *ctx, int m_p, double *k_over_d2,
             else
                 k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->a64[0].p, nullptr, 1, scratch);
         } else {
-            if (is_f32(ctx)) CK(lbm_launch_macro<float>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f32[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
-            else CK(lbm_launch_macro<double>(ctx->n, ctx->npad, ctx->lbm_layout, ctx->q, ctx->f64[ctx->cur].p, ctx->gl, ctx->mac.p, ctx->st));
+            CK(lbm_macro_current(ctx));
             ++ctx->launches;
             k_probe_sum_static<double><<<(unsigned)nb, 256, 0, ctx->st>>>(ctx->np_fluid, ctx->n_l, ctx->pidx.p, ctx->pw.p, ctx->mac.p, nullptr, 4, scratch);
         }

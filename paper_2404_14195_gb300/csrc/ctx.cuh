@@ -81,6 +81,11 @@ struct rbf_ctx {
     DevArr<float> f32[2];
     DevArr<double> f64[2];
     int cur = 0;
+    // RBF_FP32R (LBM): f = f64[0] (FP64 base) + f32[cur] (FP32 correction); f64[1] is
+    // scratch; rr the FP32 residual of the last refresh; a refresh every refine_m
+    // steps, refine_phase steps since the last one
+    DevArr<float> rr;
+    int refine_m = 64, refine_phase = 0;
     // probes
     int m_p = 0;
     int64_t np_fluid = 0;
@@ -92,7 +97,7 @@ struct rbf_ctx {
     DevArr<int32_t> status;
     // graph of `gsteps` steps
     cudaGraphExec_t gexec = nullptr;
-    int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1;
+    int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1, gphase = -1;
     int variant = rbf::LBM_PAIR_PER_WARP;  // schedule of the fused LBM step
     int lbm_layout = rbf::LBM_LAYOUT_PAIRS;  // layout of f32 / f64 (follows the schedule)
     int acm_block = 256;              // threads per block of the ACM sweeps

@@ -101,6 +101,11 @@ cudaError_t launch_pack_f32(int64_t nc, int n_ops, int o0, int n_out, int n_l, c
 cudaError_t launch_pack_f64(int64_t nc, int n_ops, int o0, int n_out, int n_l, const double *w, double *ws,
                             cudaStream_t st);
 cudaError_t launch_pack_idx(int64_t nc, int n_l, const int32_t *idx, int32_t *is, cudaStream_t st);
+// FP32 copies of weight rows with each row's exact sum kept (values returned as
+// doubles); wall normal-derivative rows [nb][n_l] in FP64
+cudaError_t launch_round_rows_f32(int64_t nrows, int n_l, const double *w, double *out, cudaStream_t st);
+cudaError_t launch_normal_rows(int64_t nb, int n_l, const int32_t *wall, const double *nrm, const double *wg,
+                               double *out, cudaStream_t st);
 // wall normal-derivative weights n . (wx, wy, wz) -> SELL T
 cudaError_t launch_pack_normal_f32(int64_t nb, int n_l, const int32_t *wall, const double *nrm,
                                    const double *wg, float *ws, cudaStream_t st);

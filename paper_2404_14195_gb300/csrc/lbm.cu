@@ -152,8 +152,9 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// One thread per node: all q populations of the node in registers.
-template <typename T, int Q>
+// One thread per node: all q populations of the node in registers.  RA: add the
+// residual a.radd to the post-collision populations (refined FP32).
+template <typename T, int Q, bool RA = false>
 __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
     using V = typename Vec2<T>::type;
     constexpr int NP = (Q - 1) / 2;
@@ -187,6 +188,16 @@ __global__ void __launch_bounds__(256) k_lbm_step(LbmArgs<T> a) {
             if (m & (1u << k)) f[k] = f[opp(k)];
     }
     trt_collide<T, Q>(f, a.tp_inv, a.tm_inv, a.gx, a.gy, a.gz);
+    if constexpr (RA) {
+        f[0] += a.radd[i];
+        const V *__restrict__ r2 = reinterpret_cast<const V *>(a.radd + np);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const V r = r2[p * np + i];
+            f[2 * p + 1] += r.x;
+            f[2 * p + 2] += r.y;
+        }
+    }
     a.fout[i] = f[0];
     V *__restrict__ op2 = reinterpret_cast<V *>(a.fout + np);
 #pragma unroll
@@ -219,7 +230,7 @@ template <> struct Vec16<double> {
 // i.e. a register cap (FP32: 4 -> 64 registers, no spills; 5 -> 48 registers, a
 // few spills, more warps in flight).  Same arithmetic, in the same order, as
 // k_lbm_step.
-template <typename T, int Q, int MINB>
+template <typename T, int Q, int MINB, bool RA = false>
 __global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
     using V = typename Vec2<T>::type;
     using W = Vec16<T>;
@@ -264,6 +275,16 @@ __global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
     for (int k = 0; k < Q; ++k) o[k] = f[k];
 #pragma unroll
     for (int k = Q; k < RL; ++k) o[k] = (T)0;
+    if constexpr (RA) {
+        const V16 *__restrict__ rr = reinterpret_cast<const V16 *>(a.radd) + i * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            T r[W::n];
+            W::get(rr[v], r);
+#pragma unroll
+            for (int t = 0; t < W::n; ++t) o[v * W::n + t] += r[t];
+        }
+    }
     V16 *__restrict__ out = reinterpret_cast<V16 *>(a.fout) + i * NV;
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v] = W::make(o + v * W::n);
@@ -280,7 +301,7 @@ __global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
 // memory (populations and weights), so each stencil column costs one 8-byte
 // gather and one 256-byte coalesced weight row per warp; the loop is unrolled U
 // deep to keep U such requests in flight per thread.
-template <typename T, int Q, int U>
+template <typename T, int Q, int U, bool RA = false>
 __global__ void __launch_bounds__(32 * ((Q - 1) / 2), sizeof(T) == 4 ? 5 : 2) k_lbm_step_pairs(LbmArgs<T> a) {
     using V = typename Vec2<T>::type;
     constexpr int NP = (Q - 1) / 2;
@@ -360,10 +381,17 @@ __global__ void __launch_bounds__(32 * ((Q - 1) / 2), sizeof(T) == 4 ? 5 : 2) k_
     V o;
     o.x = ak - dp - dm + F;
     o.y = ab - dp + dm - F;
+    if constexpr (RA) {
+        const V r = reinterpret_cast<const V *>(a.radd + np)[(int64_t)w * np + i];
+        o.x += r.x;
+        o.y += r.y;
+    }
     reinterpret_cast<V *>(a.fout + np)[(int64_t)w * np + i] = o;
     if (w == 0) {
         const T feq0 = (T)VSet<Q>::w(0) * (drho + base);
-        a.fout[i] = f0 - (f0 - feq0) * tp_inv;
+        T f0n = f0 - (f0 - feq0) * tp_inv;
+        if constexpr (RA) f0n += a.radd[i];
+        a.fout[i] = f0n;
     }
 }
 
@@ -464,23 +492,23 @@ cudaError_t lbm_launch_pack_f64(int64_t nc, int q, int n_l, const double *w, dou
     return cudaGetLastError();
 }
 
-template <typename T, int Q>
+template <typename T, int Q, bool RA>
 static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code) {
     constexpr int NP = (Q - 1) / 2;
     const unsigned slices = (unsigned)(a.npad >> 5);
     switch (code) {
-    case LBM_NODE_PER_THREAD: k_lbm_step<T, Q><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a); break;
-    case LBM_NODE_PER_THREAD_128: k_lbm_step<T, Q><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a); break;
-    case LBM_PAIR_PER_WARP: k_lbm_step_pairs<T, Q, 5><<<slices, 32 * NP, 0, st>>>(a); break;
-    case LBM_PAIR_PER_WARP_U3: k_lbm_step_pairs<T, Q, 3><<<slices, 32 * NP, 0, st>>>(a); break;
-    case LBM_PAIR_PER_WARP_U6: k_lbm_step_pairs<T, Q, 6><<<slices, 32 * NP, 0, st>>>(a); break;
-    case LBM_PAIR_PER_WARP_U2: k_lbm_step_pairs<T, Q, 2><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_NODE_PER_THREAD: k_lbm_step<T, Q, RA><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a); break;
+    case LBM_NODE_PER_THREAD_128: k_lbm_step<T, Q, RA><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP: k_lbm_step_pairs<T, Q, 5, RA><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U3: k_lbm_step_pairs<T, Q, 3, RA><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U6: k_lbm_step_pairs<T, Q, 6, RA><<<slices, 32 * NP, 0, st>>>(a); break;
+    case LBM_PAIR_PER_WARP_U2: k_lbm_step_pairs<T, Q, 2, RA><<<slices, 32 * NP, 0, st>>>(a); break;
     // register caps: FP32 64 / 48 (4 / 5 blocks per SM); FP64 128 / 80 (2 / 3 blocks)
     case LBM_RECORD_PER_THREAD:
-        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2, RA><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
         break;
     case LBM_RECORD_PER_THREAD_OCC:
-        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 5 : 3><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 5 : 3, RA><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -490,9 +518,52 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
 template <typename T>
 cudaError_t lbm_launch_step(const LbmArgs<T> &a, int q, cudaStream_t st, int code) {
     if (code < 0 || code >= LBM_N_SCHEDULES || lbm_layout_of(code) != a.layout) return cudaErrorInvalidValue;
-    if (q == 19) return launch_step_q<T, 19>(a, st, code);
-    if (q == 15) return launch_step_q<T, 15>(a, st, code);
+    if (a.radd) {  // the residual addend: refined FP32 only
+        if constexpr (sizeof(T) == 4) {
+            if (q == 19) return launch_step_q<T, 19, true>(a, st, code);
+            if (q == 15) return launch_step_q<T, 15, true>(a, st, code);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (q == 19) return launch_step_q<T, 19, false>(a, st, code);
+    if (q == 15) return launch_step_q<T, 15, false>(a, st, code);
     return cudaErrorInvalidValue;
+}
+
+// ---- refined FP32: f = base (FP64) + delta (FP32) -------------------------------
+__global__ void k_refine_fold(int64_t tot, double *__restrict__ base, const float *__restrict__ delta) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < tot) base[e] += (double)delta[e];
+}
+__global__ void k_refine_residual(int64_t tot, const double *__restrict__ fnew, const double *__restrict__ base,
+                                  float *__restrict__ r, float *__restrict__ delta) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    const float v = (float)(fnew[e] - base[e]);
+    r[e] = v;
+    delta[e] = v;
+}
+__global__ void k_refine_combine(int64_t tot, const double *__restrict__ base, const float *__restrict__ delta,
+                                 double *__restrict__ out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < tot) out[e] = base[e] + (double)delta[e];
+}
+cudaError_t lbm_launch_refine_fold(int64_t tot, double *base, const float *delta, cudaStream_t st) {
+    if (tot == 0) return cudaSuccess;
+    k_refine_fold<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, base, delta);
+    return cudaGetLastError();
+}
+cudaError_t lbm_launch_refine_residual(int64_t tot, const double *fnew, const double *base, float *r, float *delta,
+                                       cudaStream_t st) {
+    if (tot == 0) return cudaSuccess;
+    k_refine_residual<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, fnew, base, r, delta);
+    return cudaGetLastError();
+}
+cudaError_t lbm_launch_refine_combine(int64_t tot, const double *base, const float *delta, double *out,
+                                      cudaStream_t st) {
+    if (tot == 0) return cudaSuccess;
+    k_refine_combine<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(tot, base, delta, out);
+    return cudaGetLastError();
 }
 
 template <typename T>

@@ -22,6 +22,9 @@ struct LbmArgs {
     T *fout;
     T tp_inv, tm_inv;      // 1/tau+, 1/tau-
     T gx, gy, gz;          // g_lb
+    // refined FP32 (RBF_FP32R): the residual r added to every post-collision
+    // population (same layout as fout), else null; FP32 only
+    const T *radd = nullptr;
 };
 
 const int *host_velocity_set(int q);
@@ -64,5 +67,13 @@ cudaError_t lbm_launch_import(int64_t n, int64_t npad, int layout, int q, T *f, 
 template <typename T>
 cudaError_t lbm_launch_macro(int64_t n, int64_t npad, int layout, int q, const T *f, const double g[3], double *out,
                              cudaStream_t st);
+// refined FP32 state f = base (FP64) + delta (FP32), elementwise over `tot` stored
+// values (either layout, padding included): base += delta; r = fl(fnew - base) and
+// delta = r; out = base + delta
+cudaError_t lbm_launch_refine_fold(int64_t tot, double *base, const float *delta, cudaStream_t st);
+cudaError_t lbm_launch_refine_residual(int64_t tot, const double *fnew, const double *base, float *r, float *delta,
+                                       cudaStream_t st);
+cudaError_t lbm_launch_refine_combine(int64_t tot, const double *base, const float *delta, double *out,
+                                      cudaStream_t st);
 
 }  // namespace rbf

@@ -322,6 +322,61 @@ cudaError_t launch_weights(int64_t nc, const double *xyz, const double *cxyz, co
     return cudaGetLastError();
 }
 
+// ---- FP32 copies of the weights ---------------------------------------------
+// Each row of n_l FP64 weights (one operator at one centre) is rounded to FP32 so
+// that the exact sum of the FP32 values stays at the FP64 row sum: every weight is
+// rounded to nearest, then the sum's residual is added to the smallest-magnitude
+// nonzero weight, which is rounded again (its ulp bounds what is left).  Plain
+// rounding leaves each row sum off by ~1e-7 of its weights' size, so constants
+// are no longer reproduced (interpolation rows no longer sum to 1, derivative
+// rows no longer to 0); the explicit iterations carry that error in every step
+// and in the MLBM it biased the steady permeability by 2e-4 on the 150k-node cell.
+// out holds the FP32 values as doubles (exactly representable), rows as in w.
+__global__ void k_round_rows_f32(int64_t nrows, int n_l, const double *__restrict__ w, double *__restrict__ out) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const double *a = w + r * n_l;
+    double *o = out + r * n_l;
+    double s64 = 0.0, s32 = 0.0, amin = 0.0;
+    int jmin = -1;
+    for (int j = 0; j < n_l; ++j) {
+        const float f = (float)a[j];
+        s64 += a[j];
+        s32 += (double)f;
+        o[j] = (double)f;
+        if (f != 0.0f && (jmin < 0 || fabs((double)f) < amin)) { amin = fabs((double)f); jmin = j; }
+    }
+    if (jmin >= 0) o[jmin] = (double)(float)(o[jmin] + (s64 - s32));
+}
+
+cudaError_t launch_round_rows_f32(int64_t nrows, int n_l, const double *w, double *out, cudaStream_t st) {
+    if (nrows == 0) return cudaSuccess;
+    k_round_rows_f32<<<(unsigned)((nrows + 255) / 256), 256, 0, st>>>(nrows, n_l, w, out);
+    return cudaGetLastError();
+}
+
+// wall normal-derivative rows w^n_j = n_x w^x_j + n_y w^y_j + n_z w^z_j (FP64,
+// [nb][n_l]) from the gradient weights of the wall nodes' Neumann stencils
+__global__ void k_normal_rows(int64_t nb, int n_l, const int32_t *__restrict__ wall, const double *__restrict__ nrm,
+                              const double *__restrict__ wg, double *__restrict__ out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nb * n_l) return;
+    int64_t b = t / n_l;
+    int j = (int)(t - b * n_l);
+    int64_t i = wall[b];
+    const double *g = wg + b * 3 * n_l;
+    double nx = nrm[3 * i], ny = nrm[3 * i + 1], nz = nrm[3 * i + 2];
+    out[t] = __dadd_rn(__dadd_rn(__dmul_rn(nx, g[j]), __dmul_rn(ny, g[n_l + j])), __dmul_rn(nz, g[2 * n_l + j]));
+}
+
+cudaError_t launch_normal_rows(int64_t nb, int n_l, const int32_t *wall, const double *nrm, const double *wg,
+                               double *out, cudaStream_t st) {
+    int64_t tot = nb * n_l;
+    if (tot == 0) return cudaSuccess;
+    k_normal_rows<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(nb, n_l, wall, nrm, wg, out);
+    return cudaGetLastError();
+}
+
 // ---- packing into SELL-C slices for the step kernels ------------------------
 template <typename T>
 __global__ void k_pack(int64_t nc, int n_ops, int o0, int n_out, int n_l, const double *__restrict__ w, T *ws) {

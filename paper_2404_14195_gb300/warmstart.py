@@ -19,6 +19,30 @@ N_L_DEFAULT = 25
 V_REF_DEFAULT = 2.0
 
 
+# network shape (rbf_mlp_*): five layers (fan_in, fan_out); 34 real inputs
+# zero-padded to 64, 4 real outputs padded to 16
+LAYERS = ((64, 128), (128, 128), (128, 128), (128, 128), (128, 16))
+N_FEATURES, N_OUTPUTS = 34, 4
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Initial FP32 parameter vector in the packed order of rbf_mlp_set_params
+    (per layer W row-major (fan_out x fan_in), then b): W uniform in
+    +-1/sqrt(fan_in) (fan_in of the first layer counted as its 34 real inputs),
+    b = 0; the padded input columns and output rows start, and stay, at zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for li, (fi, fo) in enumerate(LAYERS):
+        fan = N_FEATURES if li == 0 else fi
+        W = rng.uniform(-1.0, 1.0, (fo, fi)) / np.sqrt(fan)
+        if li == 0:
+            W[:, N_FEATURES:] = 0.0
+        if li == len(LAYERS) - 1:
+            W[N_OUTPUTS:, :] = 0.0
+        parts += [W.ravel(), np.zeros(fo)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def signed_distance(xyz, centre, r):
     d = np.asarray(xyz, np.float64) - np.asarray(centre, np.float64)
     d -= np.rint(d)
@@ -93,16 +117,22 @@ def solve_case(case, mlp=None, n_l=N_L_DEFAULT, precision=RBF_FP32C, tol=1e-6, m
 
 
 def permeability_history(case, mlp=None, chunk=200, max_steps=20000, n_l=N_L_DEFAULT, precision=RBF_FP32C,
-                         m_p=24, device=0, v_ref=V_REF_DEFAULT):
+                         m_p=24, device=0, v_ref=V_REF_DEFAULT, tune_steps=0, schedule=None):
     """k/d^2 after every `chunk` steps of one case from a zero start or from the
     network's prediction: [(steps, k/d^2, seconds since the start)], step 0 the
     start itself (the network's evaluation and the warm start included in the
-    time, the permeability reads excluded)."""
+    time, the permeability reads excluded).  tune_steps > 0: autotune the
+    persistent driver first (untimed, state restored); schedule: a fixed
+    persistent schedule code instead.  Returns (history, schedule code used)."""
     s = Solver(device)
     s.set_case(case)
     s.build_stencils(n_l)
     s.compute_weights(solver=0)
     s.init(precision=precision, v_ref=v_ref)
+    if schedule is not None:
+        s.set_persistent_block(schedule)
+    elif tune_steps > 0:
+        schedule = s.autotune_persistent(tune_steps)[1]
     t0 = time.perf_counter()
     if mlp is not None:
         mlp.warm_start(s, 1.0)
@@ -116,7 +146,7 @@ def permeability_history(case, mlp=None, chunk=200, max_steps=20000, n_l=N_L_DEF
         steps += chunk
         hist.append((steps, s.permeability(m_p)[0], t_run))
     s.close()
-    return hist
+    return hist, schedule
 
 
 def first_within(hist, k_ref, rel=1e-4):

@@ -177,6 +177,48 @@ def test_lbm_fp32_populations(rbf, cell, variant):
     assert rel_inf(got - om[:, None], want - om[:, None]) <= 1e-4
 
 
+@pytest.mark.parametrize("variant", [1, 0, 6, 7])
+def test_lbm_fp32r_populations(rbf, cell, variant):
+    """Refined FP32 (FP64 base + FP32 correction, one FP64 refresh every 64
+    steps): after 200 steps (four refreshes) the populations follow the oracle
+    within the FP32 bar.  The body force is the paper's scale (g = 1): the
+    correction step is the FP32 step linearised about the rest state, accurate
+    while the lattice velocities stay small."""
+    q = 19
+    g = (1.0, 0.0, 0.0)
+    s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP32R, g)
+    s.set_kernel_variant(variant)
+    tm = oracle.tau_minus(0.8, 3.0 / 16.0)
+    f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
+    n = 200
+    s.step(n)
+    fn = oracle.lbm_run(f0, q, cell, idx, wk, 0.8, tm, u["g_lb"], n)
+    want = oracle.lbm_collide(fn, q, 0.8, tm, u["g_lb"])
+    _, om, _ = oracle.velocity_set(q)
+    got = s.lbm_get_populations()
+    assert rel_inf(got - om[:, None], want - om[:, None]) <= 1e-4
+    fields = s.get_fields()
+    assert rel_inf(fields[:, :3], oracle.lbm_fields(fn, q, u)[:, :3]) <= 1e-4
+
+
+def test_lbm_fp32r_state_round_trip_and_layout_switch(rbf, cell):
+    """rbf_lbm_set_populations writes the FP64 base of a refined FP32 state (the
+    values come back to FP64 rounding), and a layout switch keeps the state."""
+    q, g = 19, (1.0, 0.0, 0.0)
+    s, u, idx, wk, dx = _lbm_case(rbf, cell, q, rbf.RBF_FP32R, g)
+    s.set_kernel_variant(1)
+    s.step(70)
+    f = s.lbm_get_populations()
+    rng = np.random.default_rng(1)
+    x = f + 1e-9 * rng.standard_normal(f.shape)
+    s.lbm_set_populations(x)
+    assert np.abs(s.lbm_get_populations() - x).max() <= 1e-15
+    s.set_kernel_variant(6)  # pairs -> node records
+    assert np.abs(s.lbm_get_populations() - x).max() <= 1e-15
+    s.step(10)
+    assert np.isfinite(s.lbm_get_populations()).all()
+
+
 @pytest.mark.parametrize("first,second", [(1, 6), (7, 0)])
 def test_lbm_layout_switch_mid_run(rbf, cell, first, second):
     """Switching between schedules of the pairs and node-record layouts rewrites

@@ -58,13 +58,18 @@ def test_inject_writes_the_scaled_network_output(rbf, prec):
 
 
 def _oracle_steady_k(case, v_ref=2.0, m_p=24):
+    """The oracle MNS's converged k/d^2 (unchanged to 1e-9 over the last 2,000 of
+    18,000 steps from rest)."""
     o = oracle_acm_setup(case, 25)
     dt = oracle.acm_dt(o["h_min"], 1.0)
-    f, res = oracle.acm_run(case, o["idx"], o["w4"], o["idxb"], o["wgb"], np.zeros((case.n, 4)), 16000, dt=dt,
-                            v_ref=v_ref)
-    assert res[-1] < 1e-13
     pr = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], m_p, 25)
-    return oracle.permeability(pr, f[:, 0], 1.0, 1.0)[0]
+    f = np.zeros((case.n, 4))
+    ks = []
+    for nsteps in (16000, 2000):
+        f, _ = oracle.acm_run(case, o["idx"], o["w4"], o["idxb"], o["wgb"], f, nsteps, dt=dt, v_ref=v_ref)
+        ks.append(oracle.permeability(pr, f[:, 0], 1.0, 1.0)[0])
+    assert abs(ks[1] - ks[0]) <= 1e-9 * ks[1]
+    return ks[1]
 
 
 def test_warm_start_reaches_the_oracle_permeability_in_fewer_steps(rbf):
@@ -81,8 +86,8 @@ def test_warm_start_reaches_the_oracle_permeability_in_fewer_steps(rbf):
     for i, r in enumerate((0.25, 0.37)):
         case = synth.jittered_cell(r=r, n_axis=12, seed=500 + i)
         k_o = _oracle_steady_k(case)
-        hz = ws.permeability_history(case, None, chunk=200, max_steps=14000)
-        hw = ws.permeability_history(case, m, chunk=200, max_steps=14000)
+        hz, _ = ws.permeability_history(case, None, chunk=200, max_steps=14000)
+        hw, _ = ws.permeability_history(case, m, chunk=200, max_steps=14000)
         z, w = ws.first_within(hz, k_o), ws.first_within(hw, k_o)
         assert z is not None and w is not None, (hz[-1], hw[-1], k_o)
         assert abs(hz[-1][1] - k_o) <= 1e-4 * k_o and abs(hw[-1][1] - k_o) <= 1e-4 * k_o
