@@ -72,7 +72,7 @@ def bytes_per_node_step(q=Q, n_l=N_L, elt=4):
 
 
 def prec_code(rbf, name):
-    return {"fp32": rbf.RBF_FP32, "fp32c": rbf.RBF_FP32C, "fp64": rbf.RBF_FP64}[name]
+    return {"fp32": rbf.RBF_FP32, "fp32c": rbf.RBF_FP32C, "fp64": rbf.RBF_FP64, "fp32r": rbf.RBF_FP32R}[name]
 
 
 def config_dict(n, nb, prec="fp32"):
@@ -228,8 +228,9 @@ def main():
                          "warm-start network training steps on the tensor cores")
     ap.add_argument("--cfg4-ramp", type=float, default=0.32, help="acm-config4 refinement ramp (0.32: ~3M nodes)")
     ap.add_argument("--cells", type=int, default=64, help="batch-config3: number of cells")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64"],
-                    help="storage and arithmetic of the steps (fp32c: compensated FP32 state, ACM workloads only)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64", "fp32r"],
+                    help="storage and arithmetic of the steps (fp32c: compensated FP32 state, ACM workloads only; "
+                         "fp32r: refined FP32 populations, the MLBM headline only)")
     ap.add_argument("--no-tts", action="store_true", help="default line without the time-to-steady block")
     ap.add_argument("--no-workloads", action="store_true",
                     help="default line without the config-4 and config-3 blocks")
@@ -238,6 +239,8 @@ def main():
     args = ap.parse_args()
     if args.precision == "fp32c" and args.workload == "lbm-config2":
         ap.error("--precision fp32c applies to the ACM workloads")
+    if args.precision == "fp32r" and args.workload != "lbm-config2":
+        ap.error("--precision fp32r applies to the MLBM headline")
     if args.workload != "lbm-config2":
         return run_workload(args)
     if args.impl == "reference":
@@ -330,7 +333,9 @@ def main():
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     elt = 8 if args.precision == "fp64" else 4
-    bpl = bytes_per_node_step(elt=elt) * n
+    # refined FP32: the profiled launches are the correction steps, which also read
+    # the residual (4 B per population)
+    bpl = (bytes_per_node_step(elt=elt) + (4 * Q if args.precision == "fp32r" else 0)) * n
     achieved = bpl / (per_launch_ms / 1e3) / 1e9
     kname = KERNELS[chosen] if elt == 4 else (KERNELS[chosen].replace("float", "double")
                                               .replace(",19,4>", ",19,2>").replace(",19,5>", ",19,3>"))
