@@ -16,7 +16,7 @@ import time
 
 import numpy as np
 
-from . import RBF_FP32C, RBF_FP64, RbfError
+from . import RBF_FP32, RBF_FP32C, RBF_FP32R, RBF_FP64, RbfError
 from . import crossval
 
 # the radii of the paper's porosity sweep run over r in [0.04, 0.69]
@@ -251,6 +251,10 @@ def main(argv=None):
     ap.add_argument("--window", type=int, default=10_000)
     ap.add_argument("--max-steps", type=int, default=4_000_000)
     ap.add_argument("--precision-acm", choices=("fp64", "fp32c"), default="fp32c")
+    ap.add_argument("--precision-lbm", choices=("fp64", "fp32", "fp32r"), default="fp64",
+                    help="MLBM populations: fp32r keeps FP32 steps on an FP64 base (RBF_FP32R)")
+    ap.add_argument("--n-l-lbm", type=int, default=None, help="MLBM stencil size (default: --n-l)")
+    ap.add_argument("--v-ref", default="auto", help='MNS reference speed: a number or "auto"')
     ap.add_argument("--solid-check-above", type=float, default=None)
     ap.add_argument("--solver", choices=("mlbm", "mns"), default="mns", help="trace: the solver")
     ap.add_argument("--v-ref-list", default="0.01", help="trace (MNS): comma-separated v_ref values")
@@ -264,7 +268,11 @@ def main(argv=None):
     dist, rank, world, local = dist_env()
     ranks = (dist, rank, world)
     kw = dict(window_steps=a.window, max_steps=a.max_steps, tune=True, device=local,
-              precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64, precision_lbm=RBF_FP64)
+              precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64,
+              precision_lbm={"fp64": RBF_FP64, "fp32": RBF_FP32, "fp32r": RBF_FP32R}[a.precision_lbm],
+              n_l_lbm=a.n_l_lbm, v_ref=a.v_ref if a.v_ref == "auto" else float(a.v_ref))
+    if a.study in ("porosity", "spread"):
+        kw["n_l"] = a.n_l
     t = time.perf_counter()
     if a.study == "porosity":
         res = porosity_sweep(radii, a.h_min, solid_check_above=a.solid_check_above, _ranks=ranks, **kw)
