@@ -33,6 +33,10 @@ Other workloads (--workload), same line format:
   batch-config3  64 cells stepped in one persistent launch
   mlp-train      warm-start network training steps (fused tensor-core kernels)
   tts-config1    the time-to-steady block alone
+  warmstart-config5  the learned warm start at the configured node counts: the
+                 network trained on steady fields of --cells cells (h = 1/40,
+                 35k-63k nodes) and evaluated on eight held-out radii against the
+                 oracle's steady k/d^2
 """
 from __future__ import annotations
 
@@ -56,7 +60,8 @@ R, H_MIN, H_MAX, RAMP, SEED = 0.40, 0.008, 0.04, 0.2, 2
 N_L, Q, DX, TAU_P, MAGIC = 30, 19, 0.004, 0.8, 3.0 / 16.0
 KERNELS = {0: "k_lbm_step<float,19> (256)", 1: "k_lbm_step_pairs<float,19,5>", 2: "k_lbm_step<float,19> (128)",
            3: "k_lbm_step_pairs<float,19,3>", 4: "k_lbm_step_pairs<float,19,6>", 5: "k_lbm_step_pairs<float,19,2>",
-           6: "k_lbm_step_records<float,19,4> (256)", 7: "k_lbm_step_records<float,19,5> (256)"}
+           6: "k_lbm_step_records<float,19,4> (256)", 7: "k_lbm_step_records<float,19,5> (256)",
+           8: "k_lbm_step_records<float,19,4> (128)", 9: "k_lbm_step_records<float,19,4> (64)"}
 
 
 def workload():
@@ -222,7 +227,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="LBM step schedule (rbf_set_kernel_variant code); -1 = autotune on the case")
     ap.add_argument("--workload", default="lbm-config2",
-                    choices=["lbm-config2", "acm-config4", "batch-config3", "mlp-train", "tts-config1"],
+                    choices=["lbm-config2", "acm-config4", "batch-config3", "mlp-train", "tts-config1",
+                             "warmstart-config5"],
                     help="lbm-config2 (default, the headline); acm-config4: ~3M-node ACM cell, r^5, m=3, N_L=40, "
                          "FP32; batch-config3: 64-cell porosity sweep in one persistent launch; mlp-train: "
                          "warm-start network training steps on the tensor cores")
@@ -481,6 +487,8 @@ def run_workload(args):
         line = _batch_config3(args, rbf, local, dist, ws, peaks, cells3)
     elif args.workload == "tts-config1":
         line = _tts_config1(args, rbf, local)
+    elif args.workload == "warmstart-config5":
+        line = _warmstart_config5(args, rbf, local)
     else:
         line = _mlp_train(args, rbf, local, dist, ws, peaks)
     if rank == 0:
@@ -854,6 +862,75 @@ def _tts_mlbm_config2(rbf, local, case, ref, chunk=5000, max_steps=250000, m_p=3
             "k_ref": k_ref, "k_ref_source": f"FP64 oracle, {ref['steps']} steps (tests/golden/steady_references.json)",
             "target": "first chunk after which |k - k_ref| <= 1e-4 k_ref for the rest of the run",
             "runs": runs, "clocks": clk.summary()}
+
+
+C5_HELDOUT_RADII = (0.17, 0.21, 0.25, 0.29, 0.33, 0.37, 0.41, 0.45)
+
+
+def _warmstart_config5(args, rbf, local, chunk=1000, max_steps=120000, m_p=32, v_ref=2.0, n_axis=40):
+    """What the trained network gains at the configured node counts.  Training:
+    steady compensated FP32 fields (v_ref = 2, residual 5e-8) of --cells jittered
+    cells (h = 1/40, radii U[0.15, 0.47], seeds 300+) solved in one batched
+    persistent launch, then 20,000 Adam steps of 8,192 samples.  Evaluation: eight
+    held-out radii (other seeds), each solved from rest in FP64 and in compensated
+    FP32 and from the network in compensated FP32, in chunks of 1,000 steps; the
+    target is the first chunk after which k/d^2 stays within 1e-4 of the FP64
+    oracle's steady value (tests/golden/steady_references.json) up to max_steps."""
+    import synth
+    from paper_2404_14195_gb300 import warmstart as wsm
+    refs = golden_references()
+    rng = np.random.default_rng(5)
+    train = [synth.jittered_cell(r=float(r), n_axis=n_axis, seed=300 + i)
+             for i, r in enumerate(rng.uniform(0.15, 0.47, args.cells))]
+    data, res, t_data = wsm.steady_training_set(train, tol=5e-8, max_steps=400_000, check_every=1000, v_ref=v_ref)
+    mlp, hist, t_train = wsm.train(data, wsm.init_params(1), steps=20000, batch=8192, lr=2e-3,
+                                   decay=((10000, 6e-4), (10000, 2e-4)))
+    clk = Clocks(local)
+    clk.__enter__()
+    rows, tot = [], {"fp64_zero": [0, 0.0], "fp32c_zero": [0, 0.0], "fp32c_warm": [0, 0.0]}
+    for i, r in enumerate(C5_HELDOUT_RADII):
+        ref = refs.get(f"mns_c5_heldout_{i}")
+        case = synth.jittered_cell(r=r, n_axis=n_axis, seed=900 + i)
+        if not ref or ref.get("nodes") != case.n:
+            rows.append({"r": r, "unavailable": "no oracle reference"})
+            continue
+        k_ref = ref["k_over_d2"]
+        row = {"r": r, "nodes": case.n, "k_ref": k_ref}
+        sched = {}
+        for name, prec, m in (("fp64_zero", rbf.RBF_FP64, None), ("fp32c_zero", rbf.RBF_FP32C, None),
+                              ("fp32c_warm", rbf.RBF_FP32C, mlp)):
+            h, code = wsm.permeability_history(case, m, chunk=chunk, max_steps=max_steps, precision=prec, m_p=m_p,
+                                               v_ref=v_ref, tune_steps=0 if prec in sched else 200,
+                                               schedule=sched.get(prec))
+            sched[prec] = code
+            hit = _first_within(h, k_ref)
+            row[name] = {"steps": None if hit is None else hit[0], "seconds": None if hit is None else hit[2],
+                         "k_start_rel_err": abs(h[0][1] - k_ref) / k_ref,
+                         "k_end_rel_err": abs(h[-1][1] - k_ref) / k_ref}
+            if hit is not None and tot[name] is not None:
+                tot[name][0] += hit[0]
+                tot[name][1] += hit[2]
+            else:
+                tot[name] = None
+        rows.append(row)
+    clk.__exit__(None, None, None)
+    summ = {k: (None if v is None else {"steps": v[0], "seconds": v[1]}) for k, v in tot.items()}
+    gain = None
+    if summ["fp32c_zero"] and summ["fp32c_warm"]:
+        gain = {"steps_warm_over_zero": summ["fp32c_warm"]["steps"] / summ["fp32c_zero"]["steps"],
+                "speedup_warm_fp32c_vs_fp64_zero": (summ["fp64_zero"]["seconds"] / summ["fp32c_warm"]["seconds"]
+                                                    if summ["fp64_zero"] else None)}
+    return {"metric": "time-to-steady-permeability (1e-4 rel) of held-out cells: network start vs rest",
+            "value": None if not summ["fp32c_warm"] else summ["fp32c_warm"]["seconds"], "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 compensated (+ bf16 network)", "data": "synthetic (seeded cells)",
+            "config": {"workload": f"{len(train)} training cells and {len(C5_HELDOUT_RADII)} held-out cells, jittered "
+                                   f"grid h=1/{n_axis} ({min(c.n for c in train)}-{max(c.n for c in train)} nodes), "
+                                   f"N_L=25, v_ref={v_ref}",
+                       "train_samples": int(len(data[0])), "train_data_s": t_data,
+                       "train_cells_converged": sum(x["status"] == 0 for x in res), "train_s": t_train,
+                       "final_train_loss": float(hist[-1]), "chunk": chunk, "max_steps": max_steps},
+            "totals": summ, "gain": gain, "heldout": rows, "clocks": clk.summary()}
 
 
 def _reference_workload(args):

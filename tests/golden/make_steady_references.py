@@ -9,7 +9,8 @@ one window, and records k, K, the steps taken and the last window's change.
 
   python tests/golden/make_steady_references.py [name ...]   (default: all)
 
-The config-2 MLBM entry takes about an hour on 8 cores.
+The config-2 MLBM entry takes about an hour on 8 cores, each held-out entry of
+the warm-start experiment a few minutes.
 """
 from __future__ import annotations
 
@@ -101,6 +102,15 @@ ENTRIES = {
         case=dict(kind="refined", r=0.4, h_min=0.008, h_max=0.04, ramp=0.2, seed=2),
         run=lambda c: _mlbm(c, 30, 19, 0.004, 32, 10000, 2e-8, 600000)),
 }
+
+# Held-out cells of the warm-start experiment at the configured node counts:
+# jittered grid h = 1/40 (35k-62k nodes), eight radii not drawn for training,
+# MNS at v_ref = 2
+HELDOUT_RADII = (0.17, 0.21, 0.25, 0.29, 0.33, 0.37, 0.41, 0.45)
+for _i, _r in enumerate(HELDOUT_RADII):
+    ENTRIES[f"mns_c5_heldout_{_i}"] = dict(
+        case=dict(kind="jittered", r=_r, n_axis=40, seed=900 + _i),
+        run=lambda c: _mns(c, 25, 2.0, 32, 4000, 1e-9, 400000))
 
 
 def make_case(spec):
