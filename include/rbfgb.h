@@ -259,7 +259,8 @@ int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classe
  * pairs; 6 and 7 keep each node's q populations in one record of q rounded up
  * to a multiple of 4 values, read with 16-byte loads: 6 one node per thread,
  * 256-thread blocks; 7 the same with registers capped so that five blocks fit
- * on an SM.  Switching between the two layouts on an initialised LBM
+ * on an SM; 8 and 9 as 6 in blocks of 128 and 64 threads (finer blocks spread
+ * the nodes more evenly over the SMs).  Switching between the two layouts on an initialised LBM
  * context rewrites the state (one kernel launch); the populations, as
  * rbf_lbm_get_populations reports them, are unchanged. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
@@ -275,7 +276,7 @@ typedef struct {
 } rbf_tune_report;
 
 /* Autotuner: time every candidate schedule of the step kernels on this
- * context's own case (LBM: the six fused-step schedules; ACM: 256, 128 and 64
+ * context's own case (LBM: the ten fused-step schedules; ACM: 256, 128 and 64
  * threads per block for the sweeps), trial_steps steps each with CUDA events on
  * the context stream, keep the fastest.  The fields are saved before and restored
  * after the trials, so the state and step count are unchanged.  Needs rbf_init;

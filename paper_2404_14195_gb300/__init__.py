@@ -329,8 +329,8 @@ class Solver:
         """LBM step schedule: 0 / 2 one node per thread (256 / 128 threads per
         block); 1 / 3 / 4 / 5 one population pair per warp, unrolled 5 / 3 / 6 / 2;
         6 / 7 one node per thread on the node-record layout (256 threads;
-        registers capped for five blocks per SM).  The state is rewritten when the
-        layout changes."""
+        registers capped for five blocks per SM); 8 / 9 as 6 with 128 / 64
+        threads per block.  The state is rewritten when the layout changes."""
         self._ck(self._L.rbf_set_kernel_variant(self._h, int(variant)))
 
     def autotune(self, trial_steps: int = 50):

@@ -510,6 +510,12 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
     case LBM_RECORD_PER_THREAD_OCC:
         k_lbm_step_records<T, Q, sizeof(T) == 4 ? 5 : 3, RA><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
         break;
+    case LBM_RECORD_PER_THREAD_128:
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2, RA><<<(unsigned)((a.n + 127) / 128), 128, 0, st>>>(a);
+        break;
+    case LBM_RECORD_PER_THREAD_64:
+        k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2, RA><<<(unsigned)((a.n + 63) / 64), 64, 0, st>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

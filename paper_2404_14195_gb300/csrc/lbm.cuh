@@ -38,7 +38,10 @@ double host_lattice_weight(int q, int k);
 enum {
     LBM_NODE_PER_THREAD = 0, LBM_PAIR_PER_WARP = 1, LBM_NODE_PER_THREAD_128 = 2,
     LBM_PAIR_PER_WARP_U3 = 3, LBM_PAIR_PER_WARP_U6 = 4, LBM_PAIR_PER_WARP_U2 = 5,
-    LBM_RECORD_PER_THREAD = 6, LBM_RECORD_PER_THREAD_OCC = 7, LBM_N_SCHEDULES = 8
+    LBM_RECORD_PER_THREAD = 6, LBM_RECORD_PER_THREAD_OCC = 7,
+    // node layout, node per thread, 64-register kernel in blocks of 128 / 64 threads (finer
+    // blocks spread the nodes more evenly over the SMs in a one-wave launch)
+    LBM_RECORD_PER_THREAD_128 = 8, LBM_RECORD_PER_THREAD_64 = 9, LBM_N_SCHEDULES = 10
 };
 __host__ __device__ constexpr int lbm_layout_of(int schedule) {
     return schedule >= LBM_RECORD_PER_THREAD ? LBM_LAYOUT_NODES : LBM_LAYOUT_PAIRS;

@@ -81,10 +81,27 @@ def dist_env():
     return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# where each finished run is appended as one JSON line (set by main's --progress), so
+# that a long study that is stopped keeps the runs it finished
+PROGRESS_PATH = None
+
+
+def _record(i, item, result):
+    if PROGRESS_PATH is None:
+        return
+    import json
+    with open(PROGRESS_PATH, "a") as f:
+        f.write(json.dumps(crossval._jsonable(dict(index=i, item=item, result=result))) + "\n")
+
+
 def run_sharded(fn, items, dist=None, rank: int = 0, world: int = 1):
     """fn(item) for the items i with i % world == rank, then every rank gets all
     results in item order (all_gather_object of the per-rank lists)."""
-    mine = [(i, fn(x)) for i, x in enumerate(items) if i % world == rank]
+    mine = []
+    for i, x in enumerate(items):
+        if i % world == rank:
+            mine.append((i, fn(x)))
+            _record(i, x, mine[-1][1])
     if dist is None or world == 1:
         return [r for _, r in mine]
     parts = [None] * world
@@ -263,10 +280,16 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=50_000)
     ap.add_argument("--chunks", type=int, default=4)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--progress", default=None,
+                    help="append each finished run of a porosity sweep or seed spread here as a JSON line "
+                         "(per rank: the rank number is added to the name)")
     a = ap.parse_args(argv)
     radii = tuple(float(x) for x in a.radii.split(",")) if a.radii else SWEEP_RADII
     dist, rank, world, local = dist_env()
     ranks = (dist, rank, world)
+    global PROGRESS_PATH
+    if a.progress:
+        PROGRESS_PATH = a.progress if world == 1 else f"{a.progress}.{rank}"
     kw = dict(window_steps=a.window, max_steps=a.max_steps, tune=True, device=local,
               precision_acm=RBF_FP32C if a.precision_acm == "fp32c" else RBF_FP64,
               precision_lbm={"fp64": RBF_FP64, "fp32": RBF_FP32, "fp32r": RBF_FP32R}[a.precision_lbm],
