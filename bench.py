@@ -46,7 +46,6 @@ import json
 import os
 import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -92,51 +91,56 @@ def config_dict(n, nb, prec="fp32"):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi clock and throttle samples during a region.  A background thread
+    runs one-shot queries back to back (each process exits, so no sample is lost to
+    output buffering; ~10 samples per second); __enter__ returns after the first
+    sample, so the region that follows is covered."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
-        self.proc = None
-        # raw samples; BENCH_CLOCKS_DIR keeps them somewhere of the caller's choosing
-        d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
+        self.rows = []
+        self.ok = False
+        self._stop = None
+        self._thread = None
+
+    def _query(self):
+        r = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+        return [[x.strip() for x in line.split(",")] for line in r.stdout.splitlines() if line.count(",") >= 8]
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.rows += self._query()
+            except Exception:
+                return
 
     def __enter__(self):
+        import threading
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
-            # nvidia-smi takes a moment to start: wait (up to 5 s) for its first sample
-            # so that the window that follows is covered
-            t0 = time.time()
-            while time.time() - t0 < 5.0 and self.proc.poll() is None and os.path.getsize(self.path) == 0:
-                time.sleep(0.02)
+            self.rows += self._query()
+            self.ok = True
         except Exception:
-            self.proc = None
+            self.ok = False
+            return self
+        self._stop = threading.Event()
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
         return self
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            self.f.close()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=15)
 
     def summary(self):
-        if not self.proc:
+        if not self.ok:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) >= 9:
-                rows.append(p)
+        rows = [r for r in self.rows if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
