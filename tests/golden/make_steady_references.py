@@ -104,13 +104,14 @@ ENTRIES = {
 }
 
 # Held-out cells of the warm-start experiment at the configured node counts:
-# jittered grid h = 1/40 (35k-62k nodes), eight radii not drawn for training,
-# MNS at v_ref = 2
-HELDOUT_RADII = (0.17, 0.21, 0.25, 0.29, 0.33, 0.37, 0.41, 0.45)
+# jittered grid h = 1/40 (41k-58k nodes), five radii inside the training range
+# and not drawn for it, MNS at v_ref = 2.  (Radii below ~0.25 relax with time
+# constants of ~2e4 steps at this resolution; their oracle runs take hours.)
+HELDOUT_RADII = (0.29, 0.33, 0.37, 0.41, 0.45)
 for _i, _r in enumerate(HELDOUT_RADII):
     ENTRIES[f"mns_c5_heldout_{_i}"] = dict(
         case=dict(kind="jittered", r=_r, n_axis=40, seed=900 + _i),
-        run=lambda c: _mns(c, 25, 2.0, 32, 4000, 1e-9, 400000))
+        run=lambda c: _mns(c, 25, 2.0, 32, 4000, 1e-8, 400000))
 
 
 def make_case(spec):
