@@ -871,7 +871,7 @@ def _tts_mlbm_config2(rbf, local, case, ref, chunk=5000, max_steps=250000, m_p=3
 C5_HELDOUT_RADII = (0.29, 0.33, 0.37, 0.41, 0.45)
 
 
-def _warmstart_config5(args, rbf, local, chunk=1000, max_steps=80000, m_p=32, v_ref=2.0, n_axis=40):
+def _warmstart_config5(args, rbf, local, chunk=1000, max_steps=100000, m_p=32, v_ref=2.0, n_axis=40):
     """What the trained network gains at the configured node counts.  Training:
     steady compensated FP32 fields (v_ref = 2, residual 5e-8) of --cells jittered
     cells (h = 1/40, radii U[0.25, 0.47], seeds 300+) solved in one batched

@@ -335,3 +335,55 @@ def test_autotune_keeps_state_and_parity(rbf, cell, orc_acm, solver):
         got = s.get_fields()
         for c in range(4):
             assert rel_inf(got[:, c], want[:, c]) <= 1e-9, c
+
+
+@pytest.mark.parametrize("k,m", [(5, 4), (3, 2)])
+def test_acm_at_the_largest_stencil(rbf, cell, k, m):
+    """The library's maximum sizes: N_L = 64 nearest neighbours and monomials up
+    to degree 4 (saddle systems of 64 + 35 = 99 unknowns).  Weights norm-wise per
+    node and operator within 1e-10 of the oracle, then 20 FP64 steps of the
+    per-sweep kernels and of the persistent driver within 1e-9 of the oracle."""
+    n_l = 64
+    s, rep = make_solver(rbf, cell, n_l, rbf.RBF_SOLVER_ACM, k=k, m=m)
+    assert rep["n_singular"] == 0
+    idx = oracle.knn(cell["xyz"], cell["xyz"], n_l)
+    assert np.array_equal(s.get_stencils(), idx)
+    w4 = oracle.acm_weights(cell["xyz"], idx, k, m)
+    for op in range(4):
+        assert rowwise_rel(s.get_weights(op), w4[:, op]) <= 1e-10, op
+    wl, idxb = oracle.neumann_stencils(cell, n_l)
+    wgb = oracle.neumann_weights(cell, idxb, k, m)
+    dt = oracle.acm_dt(rep["h_min"], 1.0)
+    want, _ = oracle.acm_run(cell, idx, w4, idxb, wgb, np.zeros((cell.n, 4)), 20, dt=dt, v_ref=2.0)
+    s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=2.0)
+    s.step(20)
+    got = s.get_fields()
+    s.init(precision=rbf.RBF_FP64, dt=dt, v_ref=2.0)
+    assert s.solve(20, 1e-300, check_every=10)["steps"] == 20
+    got_p = s.get_fields()
+    for c in range(4):
+        assert rel_inf(got[:, c], want[:, c]) <= 1e-9, c
+        assert rel_inf(got_p[:, c], want[:, c]) <= 1e-9, c
+
+
+@pytest.mark.parametrize("variant", [1, 6])
+def test_lbm_at_the_largest_stencil(rbf, cell, variant):
+    """D3Q19 interpolation weights on N_L = 64 stencils (18 right-hand sides per
+    node) within 1e-10 of the oracle, and 20 FP64 steps within 1e-9."""
+    q, n_l, dx = 19, 64, 0.5 / 14
+    g = (2e4, 5e3, 0.0)
+    s, _ = make_solver(rbf, cell, n_l, rbf.RBF_SOLVER_LBM, q=q, dx=dx)
+    idx = oracle.knn(cell["xyz"], cell["xyz"], n_l)
+    wk = oracle.lbm_weights(cell["xyz"], idx, q, dx)
+    for kk in (1, 8, 18):
+        assert rowwise_rel(s.get_weights(rbf.RBF_OP_LBM0 + kk), wk[:, kk]) <= 1e-10, kk
+    s.init(precision=rbf.RBF_FP64, nu=1.0, g=g, tau_plus=0.8, magic=3.0 / 16.0)
+    s.set_kernel_variant(variant)
+    s.step(20)
+    u = oracle.lbm_units(1.0, 0.8, dx, g)
+    tm = oracle.tau_minus(0.8, 3.0 / 16.0)
+    f0 = oracle.lbm_equilibrium(q, np.ones(cell.n), np.zeros((cell.n, 3)))
+    fn = oracle.lbm_run(f0, q, cell, idx, wk, 0.8, tm, u["g_lb"], 20)
+    want = oracle.lbm_collide(fn, q, 0.8, tm, u["g_lb"])
+    _, om, _ = oracle.velocity_set(q)
+    assert rel_inf(s.lbm_get_populations() - om[:, None], want - om[:, None]) <= 1e-9
