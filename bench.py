@@ -592,7 +592,7 @@ def _acm_config4(args, rbf, local, dist, ws, peaks):
         "config": {"workload": f"ACM {args.precision.upper()} steps, periodic SC cell r={c['r']}, h(d)={c['h_min']}..{c['h_max']} "
                                f"ramp {args.cfg4_ramp}, N={n} ({nb} wall), N_L={L}, PHS r^{c['k']} + m={c['m']}",
                    "nodes": n, "wall_nodes": nb, "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}",
-                   "weights_solve_s": t_w, "h_min": rep["h_min"], "acm_block": chosen, "autotune": tune},
+                   "weights_solve_s": t_w, "h_min": rep["h_min"], "acm_schedule": chosen, "autotune": tune},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "traffic": None, "kernel": f"k_acm_{dom}<{tname}{cp}>", "per_kernel": per_kernel,
                      "step_GBs": step_gbs, "step_frac": step_gbs / peak},

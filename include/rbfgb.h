@@ -262,22 +262,27 @@ int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classe
  * on an SM; 8 and 9 as 6 in blocks of 128 and 64 threads (finer blocks spread
  * the nodes more evenly over the SMs).  Switching between the two layouts on an initialised LBM
  * context rewrites the state (one kernel launch); the populations, as
- * rbf_lbm_get_populations reports them, are unchanged. */
+ * rbf_lbm_get_populations reports them, are unchanged.
+ * On a context whose weights were computed for RBF_SOLVER_ACM the code selects the
+ * mapping of the ACM sweeps of rbf_step instead: block + 1000 G, with block =
+ * 64, 128 or 256 threads and G = 2 or 4 lanes per node, each lane summing every
+ * G-th stencil column (write 0 for one lane per node, i.e. the code is the block
+ * size; default 256).  RBF_EINVAL for any other code. */
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant);
 
 #define RBF_TUNE_MAX 16
 typedef struct {
     int solver;          /* RBF_SOLVER_ACM or RBF_SOLVER_LBM */
     int n_candidates;
-    int code[RBF_TUNE_MAX];  /* LBM: schedule codes of rbf_set_kernel_variant; ACM: threads per block
-                                (rbf_autotune) or persistent schedule codes (rbf_autotune_persistent) */
+    int code[RBF_TUNE_MAX];  /* schedule codes of rbf_set_kernel_variant (rbf_autotune; LBM or
+                                ACM) or persistent schedule codes (rbf_autotune_persistent) */
     double ms_per_step[RBF_TUNE_MAX];
     int chosen;          /* the fastest candidate, now in use */
 } rbf_tune_report;
 
 /* Autotuner: time every candidate schedule of the step kernels on this
- * context's own case (LBM: the ten fused-step schedules; ACM: 256, 128 and 64
- * threads per block for the sweeps), trial_steps steps each with CUDA events on
+ * context's own case (LBM: the ten fused-step schedules; ACM: the sweep codes
+ * 256, 128, 64, 2128, 2256, 4128, 4256 of rbf_set_kernel_variant), trial_steps steps each with CUDA events on
  * the context stream, keep the fastest.  The fields are saved before and restored
  * after the trials, so the state and step count are unchanged.  Needs rbf_init;
  * allocates a temporary copy of the state.  2 <= trial_steps <= 2000. */

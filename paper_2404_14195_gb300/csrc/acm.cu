@@ -1,6 +1,7 @@
 // acm.cu — explicit artificial-compressibility Navier-Stokes step (MNS section,
 // Eqs. MNS_intermediate, MNS_pressure, MNS_velocity, MNS_C; MNS algorithm of the
-// appendix), one thread per node in SELL-C slices of 32 Morton-ordered nodes.
+// appendix), on SELL-C slices of 32 Morton-ordered nodes with one or G lanes per
+// node.
 //
 // Per step:   predict  v' = v + dt (nu lap v - (v . grad) v + g)   fluid; v' = 0 walls
 //             n_p x {  pressure  p -= dt C^2 rho div v            fluid
@@ -24,30 +25,62 @@
 
 namespace rbf {
 
-template <typename T, bool CP>
+// Thread -> (node, stencil lanes): each warp is one unit of 32 / G nodes of a
+// slice; unit `sub` of slice s holds the slice's nodes sub (32 / G) .. + 32 / G - 1,
+// node nl of the unit on lanes G (nl mod 32 / G) .. + G - 1, and lane g of a node's
+// group takes the stencil columns j = g, g + G, ...; the partial sums meet in
+// group_sum and the group's first lane (g = 0) writes.  G = 1 is one node per
+// thread.  No lane returns before the shuffles.
+template <int G>
+struct NodeMap {
+    int64_t t, s, i;
+    int nl, g;
+    __device__ __forceinline__ NodeMap() {
+        t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t unit = t >> 5;
+        const int lane = (int)(t & 31);
+        s = unit / G;
+        nl = (int)(unit % G) * (32 / G) + lane / G;
+        g = lane % G;
+        i = (s << 5) + nl;
+    }
+};
+
+template <typename T, bool CP, int G>
 __global__ void __launch_bounds__(256) k_acm_predict(AcmArgs<T> a) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    if (a.type[i]) {
+    const NodeMap<G> m;
+    const int64_t i = m.i;
+    const bool valid = i < a.n;
+    const bool fluid = valid && !a.type[i];
+    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
+    if (fluid) {
+        const int n_l = a.n_l;
+        const int32_t *__restrict__ ip = a.idx + ((m.s * n_l) << 5) + m.nl;
+        const T *__restrict__ wp = a.w + ((m.s * 4 * (int64_t)n_l) << 5) + m.nl;
+#pragma unroll 5
+        for (int j = m.g; j < n_l; j += G) {
+            int q = __ldcs(ip + (j << 5));
+            T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5));
+            T wz = __ldcs(wp + ((2 * n_l + j) << 5)), wl = __ldcs(wp + ((3 * n_l + j) << 5));
+            T uq = a.u[q], vq = a.v[q], wq = a.w_[q];
+            gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
+            gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
+            gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            gu[k] = group_sum<T, G>(gu[k]);
+            gv[k] = group_sum<T, G>(gv[k]);
+            gw[k] = group_sum<T, G>(gw[k]);
+        }
+    }
+    if (!valid || m.g != 0) return;
+    if (!fluid) {
         a.us[i] = (T)0; a.vs[i] = (T)0; a.ws[i] = (T)0;
         if constexpr (CP) { a.usl[i] = (T)0; a.vsl[i] = (T)0; a.wsl[i] = (T)0; }
         return;
-    }
-    const int64_t s = i >> 5;
-    const int lane = (int)(i & 31);
-    const int n_l = a.n_l;
-    const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
-    const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
-    T gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0}, gw[4] = {0, 0, 0, 0};
-#pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
-        int q = __ldcs(ip + (j << 5));
-        T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5));
-        T wz = __ldcs(wp + ((2 * n_l + j) << 5)), wl = __ldcs(wp + ((3 * n_l + j) << 5));
-        T uq = a.u[q], vq = a.v[q], wq = a.w_[q];
-        gu[0] += wx * uq; gu[1] += wy * uq; gu[2] += wz * uq; gu[3] += wl * uq;
-        gv[0] += wx * vq; gv[1] += wy * vq; gv[2] += wz * vq; gv[3] += wl * vq;
-        gw[0] += wx * wq; gw[1] += wy * wq; gw[2] += wz * wq; gw[3] += wl * wq;
     }
     T ui = a.u[i], vi = a.v[i], wi = a.w_[i];
     T adv_u = ui * gu[0] + vi * gu[1] + wi * gu[2];
@@ -76,25 +109,28 @@ __device__ __forceinline__ double acm_C(const unsigned long long *slot, double b
     return beta * (vmax > vref ? vmax : vref);
 }
 
-template <typename T, bool CP>
+template <typename T, bool CP, int G>
 __global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__restrict__ u, const T *__restrict__ v,
                                                      const T *__restrict__ w, int read_slot, int zero_slot) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) a.vmax[zero_slot] = 0ULL;
-    if (i >= a.n || a.type[i]) return;
-    const double C = acm_C(a.vmax + read_slot, a.beta, a.vref);
-    const int64_t s = i >> 5;
-    const int lane = (int)(i & 31);
-    const int n_l = a.n_l;
-    const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
-    const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
+    const NodeMap<G> m;
+    const int64_t i = m.i;
+    if (m.t == 0) a.vmax[zero_slot] = 0ULL;
+    const bool fluid = i < a.n && !a.type[i];
     T div = 0;
+    if (fluid) {
+        const int n_l = a.n_l;
+        const int32_t *__restrict__ ip = a.idx + ((m.s * n_l) << 5) + m.nl;
+        const T *__restrict__ wp = a.w + ((m.s * 4 * (int64_t)n_l) << 5) + m.nl;
 #pragma unroll 5
-    for (int j = 0; j < n_l; ++j) {
-        int q = __ldcs(ip + (j << 5));
-        T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5)), wz = __ldcs(wp + ((2 * n_l + j) << 5));
-        div += wx * u[q] + wy * v[q] + wz * w[q];
+        for (int j = m.g; j < n_l; j += G) {
+            int q = __ldcs(ip + (j << 5));
+            T wx = __ldcs(wp + (j << 5)), wy = __ldcs(wp + ((n_l + j) << 5)), wz = __ldcs(wp + ((2 * n_l + j) << 5));
+            div += wx * u[q] + wy * v[q] + wz * w[q];
+        }
     }
+    if constexpr (G > 1) div = group_sum<T, G>(div);
+    if (!fluid || m.g != 0) return;
+    const double C = acm_C(a.vmax + read_slot, a.beta, a.vref);
     const T Ct = (T)C;
     if constexpr (CP) {
         T h = a.p[i], l = a.pl[i];
@@ -107,46 +143,57 @@ __global__ void __launch_bounds__(256) k_acm_pressure(AcmArgs<T> a, const T *__r
 
 // wall pressure from the Neumann condition, on the wall nodes' own stencils
 // {b, nearest fluid nodes}: p_b = -sum_{j>=1} w^n_j p_j / w^n_0
-template <typename T, bool CP>
+template <typename T, bool CP, int G>
 __global__ void __launch_bounds__(256) k_acm_wall_pressure(AcmArgs<T> a) {
-    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= a.nb) return;
-    const int64_t s = b >> 5;
-    const int lane = (int)(b & 31);
+    const NodeMap<G> m;
+    const int64_t b = m.i;
+    const bool valid = b < a.nb;
     const int n_l = a.n_l;
-    const int32_t *__restrict__ ip = a.idxb + ((s * n_l) << 5) + lane;
-    const T *__restrict__ wp = a.wn + ((s * n_l) << 5) + lane;
+    const int32_t *__restrict__ ip = a.idxb + ((m.s * n_l) << 5) + m.nl;
+    const T *__restrict__ wp = a.wn + ((m.s * n_l) << 5) + m.nl;
     T acc = 0;
+    if (valid) {
 #pragma unroll 4
-    for (int j = 1; j < n_l; ++j) acc += __ldcs(wp + (j << 5)) * a.p[__ldcs(ip + (j << 5))];
+        for (int j = 1 + m.g; j < n_l; j += G) acc += __ldcs(wp + (j << 5)) * a.p[__ldcs(ip + (j << 5))];
+    }
+    if constexpr (G > 1) acc = group_sum<T, G>(acc);
+    if (!valid || m.g != 0) return;
     const int32_t wb = a.wall[b];
     a.p[wb] = -acc / __ldcs(wp);
     if constexpr (CP) a.pl[wb] = (T)0;
 }
 
-template <typename T, bool CP>
+template <typename T, bool CP, int G>
 __global__ void __launch_bounds__(256) k_acm_correct(AcmArgs<T> a, int write_slot) {
     __shared__ double red[8];
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const NodeMap<G> m;
+    const int64_t i = m.i;
+    const bool valid = i < a.n;
+    const bool fluid = valid && !a.type[i];
+    T gx = 0, gy = 0, gz = 0;
+    if (fluid) {
+        const int n_l = a.n_l;
+        const int32_t *__restrict__ ip = a.idx + ((m.s * n_l) << 5) + m.nl;
+        const T *__restrict__ wp = a.w + ((m.s * 4 * (int64_t)n_l) << 5) + m.nl;
+#pragma unroll 5
+        for (int j = m.g; j < n_l; j += G) {
+            T pq = a.p[__ldcs(ip + (j << 5))];
+            gx += __ldcs(wp + (j << 5)) * pq;
+            gy += __ldcs(wp + ((n_l + j) << 5)) * pq;
+            gz += __ldcs(wp + ((2 * n_l + j) << 5)) * pq;
+        }
+    }
+    if constexpr (G > 1) {
+        gx = group_sum<T, G>(gx);
+        gy = group_sum<T, G>(gy);
+        gz = group_sum<T, G>(gz);
+    }
     double speed = 0.0;
-    if (i < a.n) {
-        if (a.type[i]) {
+    if (valid && m.g == 0) {
+        if (!fluid) {
             a.u[i] = (T)0; a.v[i] = (T)0; a.w_[i] = (T)0;
             if constexpr (CP) { a.ul[i] = (T)0; a.vl[i] = (T)0; a.wl[i] = (T)0; }
         } else {
-            const int64_t s = i >> 5;
-            const int lane = (int)(i & 31);
-            const int n_l = a.n_l;
-            const int32_t *__restrict__ ip = a.idx + ((s * n_l) << 5) + lane;
-            const T *__restrict__ wp = a.w + ((s * 4 * (int64_t)n_l) << 5) + lane;
-            T gx = 0, gy = 0, gz = 0;
-#pragma unroll 5
-            for (int j = 0; j < n_l; ++j) {
-                T pq = a.p[__ldcs(ip + (j << 5))];
-                gx += __ldcs(wp + (j << 5)) * pq;
-                gy += __ldcs(wp + ((n_l + j) << 5)) * pq;
-                gz += __ldcs(wp + ((2 * n_l + j) << 5)) * pq;
-            }
             const T f = a.dt / a.rho;
             T un, vn, wn;
             if constexpr (CP) {
@@ -185,14 +232,16 @@ __global__ void k_acm_vmax(AcmArgs<T> a, int slot) {
 
 // Iteration g of the run (counted over all steps) writes max |v| into slot g % 2;
 // the pressure sweep of iteration g reads slot (g + 1) % 2 (the previous
-// iteration's) and clears slot g % 2 for its own correction sweep.
-template <typename T, bool CP>
-cudaError_t acm_launch_step_cp(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                               LaunchRecorder *rec, int block) {
-    const unsigned gb = (unsigned)((a.n + block - 1) / block);
-    const unsigned gw = (unsigned)((a.nb + 255) / 256);
+// iteration's) and clears slot g % 2 for its own correction sweep.  The grids
+// cover every slice with G warps per slice.
+template <typename T, bool CP, int G>
+cudaError_t acm_launch_step_g(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
+                              LaunchRecorder *rec, int block) {
+    const int64_t threads = ((a.n + 31) >> 5) * 32 * G, threads_b = ((a.nb + 31) >> 5) * 32 * G;
+    const unsigned gb = (unsigned)((threads + block - 1) / block);
+    const unsigned gw = (unsigned)((threads_b + 255) / 256);
     if (rec) rec->begin(st, 0);
-    k_acm_predict<T, CP><<<gb, block, 0, st>>>(a);
+    k_acm_predict<T, CP, G><<<gb, block, 0, st>>>(a);
     if (rec) rec->end(st);
     ++*launches;
     for (int it = 0; it < n_p; ++it) {
@@ -201,32 +250,45 @@ cudaError_t acm_launch_step_cp(const AcmArgs<T> &a, int n_p, int parity, cudaStr
         const T *w = it == 0 ? a.ws : a.w_;
         const int g = (parity + it) & 1;
         if (rec) rec->begin(st, 1);
-        k_acm_pressure<T, CP><<<gb, block, 0, st>>>(a, u, v, w, g ^ 1, g);
+        k_acm_pressure<T, CP, G><<<gb, block, 0, st>>>(a, u, v, w, g ^ 1, g);
         if (rec) rec->end(st);
         ++*launches;
         if (a.nb > 0) {
             if (rec) rec->begin(st, 2);
-            k_acm_wall_pressure<T, CP><<<gw, 256, 0, st>>>(a);
+            k_acm_wall_pressure<T, CP, G><<<gw, 256, 0, st>>>(a);
             if (rec) rec->end(st);
             ++*launches;
         }
         if (rec) rec->begin(st, 3);
-        k_acm_correct<T, CP><<<gb, block, 0, st>>>(a, g);
+        k_acm_correct<T, CP, G><<<gb, block, 0, st>>>(a, g);
         if (rec) rec->end(st);
         ++*launches;
     }
     return cudaGetLastError();
 }
 
-// the compensated kernels run when the low words are present
+template <typename T, bool CP>
+cudaError_t acm_launch_step_cp(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
+                               LaunchRecorder *rec, int block, int group) {
+    switch (group) {
+    case 1: return acm_launch_step_g<T, CP, 1>(a, n_p, parity, st, launches, rec, block);
+    case 2: return acm_launch_step_g<T, CP, 2>(a, n_p, parity, st, launches, rec, block);
+    case 4: return acm_launch_step_g<T, CP, 4>(a, n_p, parity, st, launches, rec, block);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// the compensated kernels run when the low words are present; code = threads per
+// block (64, 128, 256) + 1000 x lanes per node (0 or 1: one, 2, 4)
 template <typename T>
 cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                            LaunchRecorder *rec, int block) {
-    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+                            LaunchRecorder *rec, int code) {
+    if (!acm_code_ok(code)) return cudaErrorInvalidValue;
+    const int block = code % 1000, group = code / 1000 ? code / 1000 : 1;
     const bool cp = a.ul && a.vl && a.wl && a.pl && a.usl && a.vsl && a.wsl;
     if (!cp && (a.ul || a.vl || a.wl || a.pl || a.usl || a.vsl || a.wsl)) return cudaErrorInvalidValue;
-    return cp ? acm_launch_step_cp<T, true>(a, n_p, parity, st, launches, rec, block)
-              : acm_launch_step_cp<T, false>(a, n_p, parity, st, launches, rec, block);
+    return cp ? acm_launch_step_cp<T, true>(a, n_p, parity, st, launches, rec, block, group)
+              : acm_launch_step_cp<T, false>(a, n_p, parity, st, launches, rec, block, group);
 }
 
 template <typename T>
@@ -240,10 +302,10 @@ cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st) {
 template <typename T>
 cudaError_t acm_launch_predict_only(const AcmArgs<T> &a, cudaStream_t st) {
     if (a.ul) {
-        k_acm_predict<T, true><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+        k_acm_predict<T, true, 1><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
         return cudaGetLastError();
     }
-    k_acm_predict<T, false><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
+    k_acm_predict<T, false, 1><<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -43,9 +43,24 @@ __device__ __forceinline__ void comp_add(T &hi, T &lo, T d) {
     lo = sub_rn(l, sub_rn(hi, s));
 }
 
+// Sum over the G consecutive lanes that share a node (G = 1: the value itself).
+template <typename T, int G>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// schedule code of the ACM sweeps: threads per block (64, 128, 256) + 1000 x
+// lanes per node (0 for one lane, 2 or 4)
+inline bool acm_code_ok(int code) {
+    const int block = code % 1000, group = code / 1000;
+    return code > 0 && (block == 64 || block == 128 || block == 256) && (group == 0 || group == 2 || group == 4);
+}
+
 template <typename T>
 cudaError_t acm_launch_step(const AcmArgs<T> &a, int n_p, int parity, cudaStream_t st, int64_t *launches,
-                            LaunchRecorder *rec = nullptr, int block = 256);
+                            LaunchRecorder *rec = nullptr, int code = 256);
 template <typename T>
 cudaError_t acm_launch_vmax(const AcmArgs<T> &a, int slot, cudaStream_t st);
 template <typename T>

@@ -66,14 +66,6 @@ __device__ __forceinline__ double slot_C(const unsigned long long *slot, double 
     return beta * (vmax > vref ? vmax : vref);
 }
 
-// Sum over the G consecutive lanes that share a node (G = 1: the value itself).
-template <typename T, int G>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-    for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-}
-
 // The phases work on units of 32 / G nodes of one slice: unit `sub` of slice ls
 // holds nodes sub (32 / G) .. (sub + 1) (32 / G) - 1, node nl of the unit on lanes
 // G (nl mod 32/G) .. + G - 1, each lane taking the stencil columns j = g, g + G, ...

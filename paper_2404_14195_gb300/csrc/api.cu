@@ -259,8 +259,8 @@ cudaError_t enqueue_steps(rbf_ctx *ctx, int steps, int &parity, int &cur, int64_
             continue;
         }
         if (ctx->solver == RBF_SOLVER_ACM) {
-            if (is_f32(ctx)) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
-            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_block);
+            if (is_f32(ctx)) e = acm_launch_step<float>(acm_args<float>(ctx, ctx->a32, ctx->ws32, ctx->wn32), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_code);
+            else e = acm_launch_step<double>(acm_args<double>(ctx, ctx->a64, ctx->ws64, ctx->wn64), ctx->n_p, parity, ctx->st, launches, rec, ctx->acm_code);
             parity = (parity + ctx->n_p) & 1;
         } else {
             if (rec) rec->begin(ctx->st, 0);
@@ -284,7 +284,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
     if (full > 0) {
         const int ph0 = refined ? ctx->refine_phase : 0;
         if (!ctx->gexec || ctx->gparity != ctx->parity || ctx->gcur != ctx->cur || ctx->gprec != ctx->prec ||
-            ctx->gsteps != chunk || ctx->gvariant != ctx->variant || ctx->gblock != ctx->acm_block ||
+            ctx->gsteps != chunk || ctx->gvariant != ctx->variant || ctx->gblock != ctx->acm_code ||
             ctx->gphase != ph0) {
             drop_graph(ctx);
             cudaGraph_t g;
@@ -303,7 +303,7 @@ int run_steps(rbf_ctx *ctx, int64_t nsteps) {
             ctx->gcur = ctx->cur;
             ctx->gprec = ctx->prec;
             ctx->gvariant = ctx->variant;
-            ctx->gblock = ctx->acm_block;
+            ctx->gblock = ctx->acm_code;
             ctx->gphase = ph0;
             ctx->last_kernel_launches = dummy;
         }
@@ -817,6 +817,12 @@ int rbf_last_step_timing(rbf_ctx *ctx, double *total_ms, double *kernel_ms, int6
 
 int rbf_set_kernel_variant(rbf_ctx *ctx, int variant) {
     if (!ctx) return RBF_EINVAL;
+    if (ctx->weights_ok && ctx->solver == RBF_SOLVER_ACM) {
+        if (!acm_code_ok(variant)) return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: ACM schedule code not in {64, 128, 256} + 1000 x {0, 2, 4}");
+        drop_graph(ctx);
+        ctx->acm_code = variant;
+        return RBF_OK;
+    }
     if (variant < 0 || variant >= LBM_N_SCHEDULES)
         return fail(ctx, RBF_EINVAL, "rbf_set_kernel_variant: schedule code out of range");
     DeviceGuard dg(ctx->device);
@@ -887,7 +893,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
                  LBM_PAIR_PER_WARP_U6, LBM_PAIR_PER_WARP_U2, LBM_RECORD_PER_THREAD, LBM_RECORD_PER_THREAD_OCC,
                  LBM_RECORD_PER_THREAD_128, LBM_RECORD_PER_THREAD_64};
     else
-        cands = {256, 128, 64};
+        cands = {256, 128, 64, 2128, 2256, 4128, 4256};
     rbf_tune_report r;
     std::memset(&r, 0, sizeof(r));
     double best = 1e300;
@@ -897,7 +903,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
             rc = switch_schedule(ctx, cands[c]);
             if (rc) return rc;
         } else {
-            ctx->acm_block = cands[c];
+            ctx->acm_code = cands[c];
         }
         int64_t kl = 0;
         int par = ctx->parity, cu = ctx->cur, ph = ctx->refine_phase;
@@ -923,7 +929,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
         rc = switch_schedule(ctx, best_code);
         if (rc) return rc;
     } else {
-        ctx->acm_block = best_code;
+        ctx->acm_code = best_code;
     }
     r.chosen = best_code;
     r.solver = ctx->solver;

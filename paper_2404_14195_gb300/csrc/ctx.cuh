@@ -100,7 +100,7 @@ struct rbf_ctx {
     int gsteps = 0, gparity = -1, gcur = -1, gprec = -1, gvariant = -1, gphase = -1;
     int variant = rbf::LBM_PAIR_PER_WARP;  // schedule of the fused LBM step
     int lbm_layout = rbf::LBM_LAYOUT_PAIRS;  // layout of f32 / f64 (follows the schedule)
-    int acm_block = 256;              // threads per block of the ACM sweeps
+    int acm_code = 256;               // ACM sweeps: threads per block + 1000 x lanes per node (0: one)
     int persist_block = 256;          // threads per block of the persistent ACM driver
     int persist_cluster = 0;          // > 0: run it as one cluster of that many CTAs (8 or 16)
     int persist_group = 1;            // lanes per node of its sweeps (1, 2, 4, 8)

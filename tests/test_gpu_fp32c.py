@@ -54,7 +54,10 @@ def test_fp32c_fixed_steps_multilaunch_and_persistent(rbf, cell, orc):
     c = _solver(rbf, cell, rbf.RBF_FP32C, dt=dt, v_ref=0.01)
     c.set_persistent_block(4128)  # four lanes per node
     assert c.solve(200, 1e-300, check_every=50)["steps"] == 200
-    for s in (a, b, c):
+    d = _solver(rbf, cell, rbf.RBF_FP32C, dt=dt, v_ref=0.01)
+    d.set_kernel_variant(2128)  # multi-launch sweeps, two lanes per node
+    d.step(200)
+    for s in (a, b, c, d):
         got = s.get_fields()
         for c in range(4):
             assert rel_inf(got[:, c], want[:, c]) <= 1e-4, c

@@ -78,8 +78,11 @@ def test_lbm_weights(rbf, cell, q):
         assert rowwise_rel(s.get_weights(rbf.RBF_OP_LBM0 + k), wk[:, k, :]) <= 1e-10, k
 
 
-def test_acm_fp64_fields(rbf, cell, orc_acm):
+# ACM sweep schedules: threads per block + 1000 x lanes per node
+@pytest.mark.parametrize("code", [256, 64, 2128, 2256, 4128, 4064])
+def test_acm_fp64_fields(rbf, cell, orc_acm, code):
     s, rep = make_solver(rbf, cell, 25, rbf.RBF_SOLVER_ACM)
+    s.set_kernel_variant(code)
     dt = oracle.acm_dt(orc_acm["h_min"], 1.0)
     s.init(precision=rbf.RBF_FP64, nu=1.0, g=(1.0, 0.0, 0.0), dt=dt, v_ref=0.01)
     nsteps = 200
@@ -114,8 +117,10 @@ def test_acm_set_fields_restart(rbf, cell, orc_acm):
         assert rel_inf(got[:, c], want[:, c]) <= 1e-9, c
 
 
-def test_acm_fp32_fields(rbf, cell, orc_acm):
+@pytest.mark.parametrize("code", [256, 2256, 4128])
+def test_acm_fp32_fields(rbf, cell, orc_acm, code):
     s, _ = make_solver(rbf, cell, 25, rbf.RBF_SOLVER_ACM)
+    s.set_kernel_variant(code)
     dt = oracle.acm_dt(orc_acm["h_min"], 1.0)
     s.init(precision=rbf.RBF_FP32, dt=dt, v_ref=0.01)
     s.step(200)
@@ -125,6 +130,14 @@ def test_acm_fp32_fields(rbf, cell, orc_acm):
     for c in range(4):
         assert rel_inf(got[:, c], want[:, c]) <= 1e-4, c
 
+
+
+@pytest.mark.parametrize("code", [0, 32, 512, 1256, 3128, 8128, -256])
+def test_acm_schedule_code_rejected(rbf, cell, code):
+    s, _ = make_solver(rbf, cell, 25, rbf.RBF_SOLVER_ACM)
+    with pytest.raises(rbf.RbfError) as ei:
+        s.set_kernel_variant(code)
+    assert ei.value.code == rbf.RBF_EINVAL
 
 def _lbm_case(rbf, cell, q, prec, g_phys, n_l=25):
     dx = 0.5 * (1.0 / 14)
@@ -327,7 +340,7 @@ def test_autotune_keeps_state_and_parity(rbf, cell, orc_acm, solver):
         s.step(5)
         before = s.get_fields()
         times, chosen = s.autotune(10)
-        assert set(times) == {256, 128, 64} and chosen in times
+        assert set(times) == {256, 128, 64, 2128, 2256, 4128, 4256} and chosen in times
         assert np.array_equal(s.get_fields(), before)
         s.step(25)
         want, _ = oracle.acm_run(cell, orc_acm["idx"], orc_acm["w4"], orc_acm["idxb"], orc_acm["wgb"],
