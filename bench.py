@@ -236,6 +236,8 @@ def main():
                     help="lbm-config2 (default, the headline); acm-config4: ~3M-node ACM cell, r^5, m=3, N_L=40, "
                          "FP32; batch-config3: 64-cell porosity sweep in one persistent launch; mlp-train: "
                          "warm-start network training steps on the tensor cores")
+    ap.add_argument("--mlp-batch", type=int, default=16384,
+                    help="mlp-train: samples per training step (a multiple of 128)")
     ap.add_argument("--cfg4-ramp", type=float, default=0.32, help="acm-config4 refinement ramp (0.32: ~3M nodes)")
     ap.add_argument("--cells", type=int, default=64, help="batch-config3: number of cells")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64", "fp32r"],
@@ -680,7 +682,7 @@ def _mlp_flops_per_sample():
 
 
 def _mlp_train(args, rbf, local, dist, ws, peaks):
-    B = 16384
+    B = args.mlp_batch
     rng = np.random.default_rng(0)
     n = 1 << 20
     xyz = rng.random((n, 3))

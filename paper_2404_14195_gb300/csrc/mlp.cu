@@ -390,21 +390,23 @@ __global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx,
 //    accumulator in TMEM; the epilogue (bias, GELU, GELU') writes the next layer's A
 //    operand in place and keeps H_l, GELU'(Z_l) and the output error dY in global
 //    memory for the backward kernel.
-//  k_mlp_bwd: for l = 5..1, from dZ_l (rows in shared memory, normal and
-//    transposed): dW_l = dZ_l^T H_{l-1} and dH_{l-1} = dZ_l W_l as two tcgen05 MMA
-//    chains (W_l^T resident in shared memory), dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1});
-//    the tile's dW and db are added into the gradient with vector reductions.
+//  k_mlp_bwd: for l = 5..1, from the tile's rows of dZ_l and H_{l-1} in shared
+//    memory: dW_l = dZ_l^T H_{l-1} (both tiles read MN-major, so no transposed copy
+//    is written) and dH_{l-1} = dZ_l W_l (K-major) as two tcgen05 MMA chains (W_l^T
+//    resident in shared memory), dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1}); the tile's dW
+//    and db are added into the gradient with vector reductions.
 //
-// Operands are K-major BF16 in the no-swizzle core-matrix layout with the whole K
-// in one buffer: element (r, k) of an R x K operand at byte
-// ((r/8) (K/8) + k/8) 128 + (r%8) 16 + (k%8) 2, so LBO = 128 B and SBO = 16 K B.
+// Operands are BF16 in the no-swizzle core-matrix layout with the whole K in one
+// buffer: element (r, k) of an R x K operand at byte
+// ((r/8) (K/8) + k/8) 128 + (r%8) 16 + (k%8) 2, so LBO = 128 B and SBO = 16 K B
+// read K-major; the same bytes read MN-major are the R x K tile transposed.
 // The rounding points are those of the per-layer path: BF16 features, activations,
 // GELU' and back-propagated errors, FP32 accumulation.
 constexpr int FW_WBYTES = 2 * (N_H * N_IN + 3 * N_H * N_H + N_OUT_PAD * N_H);  // W_1..W_5
 constexpr int FB_WBYTES = 2 * (3 * N_H * N_H + N_H * N_OUT_PAD);               // W_2^T..W_5^T
 constexpr int TILE_BYTES = 2 * 128 * 128;
 constexpr size_t FW_SMEM = FW_WBYTES + TILE_BYTES + 64 + 1024;
-constexpr size_t FB_SMEM = FB_WBYTES + 3 * TILE_BYTES + 4 * 128 * 4 + 64 + 1024;
+constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 64 + 1024;
 
 struct FusedArgs {
     int B;                       // rows, a multiple of 128
@@ -439,6 +441,18 @@ __device__ __forceinline__ void mma_chain(uint32_t d, const bf16 *A, const bf16 
         const uint64_t da = tc::smem_desc(reinterpret_cast<const uint8_t *>(A) + kk * 256, 128, 16 * K);
         const uint64_t db = tc::smem_desc(reinterpret_cast<const uint8_t *>(Bm) + kk * 256, 128, 16 * K);
         tc::mma_bf16(d, da, db, idesc, kk > 0 ? 1u : 0u);
+    }
+}
+
+// D (TMEM) = A^T B over the 128 rows of a tile: A and B are [128 rows][width] tiles
+// (widths wa, wb) in the K-major core layout above, read MN-major with K = the row
+// index.  Core matrices adjacent along K (8 rows) are 16 width bytes apart (LBO),
+// adjacent along M / N 128 bytes (SBO); one MMA takes 16 rows.
+__device__ __forceinline__ void mma_chain_rows(uint32_t d, const bf16 *A, int wa, const bf16 *Bm, int wb, uint32_t idesc) {
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint64_t da = tc::smem_desc(reinterpret_cast<const uint8_t *>(A) + kk * 32 * wa, 16 * wa, 128);
+        const uint64_t db = tc::smem_desc(reinterpret_cast<const uint8_t *>(Bm) + kk * 32 * wb, 16 * wb, 128);
+        tc::mma_bf16(d, da, db, idesc | tc::IDESC_A_MN | tc::IDESC_B_MN, kk > 0 ? 1u : 0u);
     }
 }
 
@@ -599,9 +613,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
         p += 2 * fan_out(l) * fan_in(l);
     }
     bf16 *An = reinterpret_cast<bf16 *>(p);                  // dZ_l [128 rows][fan_out], K = fan_out
-    bf16 *At = reinterpret_cast<bf16 *>(p + TILE_BYTES);     // dZ_l^T [fan_out][128 rows], K = 128
-    bf16 *Bt = reinterpret_cast<bf16 *>(p + 2 * TILE_BYTES); // H_{l-1}^T [fan_in][128 rows], K = 128
-    p += 3 * TILE_BYTES;
+    bf16 *Hs = reinterpret_cast<bf16 *>(p + TILE_BYTES);     // H_{l-1} [128 rows][fan_in]
+    p += 2 * TILE_BYTES;
     float *colsum = reinterpret_cast<float *>(p);             // [4 row groups][128 columns]
     p += 4 * 128 * 4;
     uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
@@ -638,7 +651,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     };
     for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
         const int64_t r = (int64_t)tile * 128 + row;
-        if (half == 0) {  // dZ_5 = dY: normal (K = 16) and transposed rows, and its column sums (db_5)
+        if (half == 0) {  // dZ_5 = dY (K = 16) and its column sums (db_5)
             __align__(16) bf16 dv[16];
             const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + r * N_OUT_PAD);
             *reinterpret_cast<uint4 *>(dv) = src[0];
@@ -647,10 +660,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             *reinterpret_cast<uint4 *>(An + cmo(row, 8, N_OUT_PAD)) = pack8(dv + 8);
             float dz[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                At[cmo(c, row, 128)] = dv[c];
-                dz[c] = __bfloat162float(dv[c]);
-            }
+            for (int c = 0; c < 16; ++c) dz[c] = __bfloat162float(dv[c]);
             colsum16(dz, 0);
         }
         __syncthreads();
@@ -660,21 +670,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
         }
         for (int l = N_LAYERS - 1; l >= 0 && ok; --l) {
             const int fi = fan_in(l), fo = fan_out(l), hw = fi >> 1;
-            {   // B_T = H_{l-1}^T (X^T for the first layer); half h: columns [h fi/2, (h+1) fi/2)
+            {   // the tile's rows of H_{l-1} (X for the first layer); half h: columns [h fi/2, (h+1) fi/2)
                 const bf16 *hin = l > 0 ? f.H[l - 1] + r * N_H : f.X + r * N_IN;
-                for (int c = hw * half; c < hw * half + hw; c += 8) {
-                    __align__(16) bf16 hv[8];
-                    *reinterpret_cast<uint4 *>(hv) = reinterpret_cast<const uint4 *>(hin)[c >> 3];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) Bt[cmo(c + i, row, 128)] = hv[i];
-                }
+                for (int c = hw * half; c < hw * half + hw; c += 8)
+                    *reinterpret_cast<uint4 *>(Hs + cmo(row, c, fi)) = reinterpret_cast<const uint4 *>(hin)[c >> 3];
             }
             smem_to_mma_sync();
             if (t == 0) {
                 if (l == N_LAYERS - 1)  // dW_5^T [128 in][16 out] = H_4^T dZ_5
-                    mma_chain(tmem + 128, Bt, At, 128, tc::idesc_bf16_f32(128, N_OUT_PAD));
+                    mma_chain_rows(tmem + 128, Hs, fi, An, N_OUT_PAD, tc::idesc_bf16_f32(128, N_OUT_PAD));
                 else                    // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}
-                    mma_chain(tmem + 128, At, Bt, 128, tc::idesc_bf16_f32(128, fi));
+                    mma_chain_rows(tmem + 128, An, fo, Hs, fi, tc::idesc_bf16_f32(128, fi));
                 if (l > 0)              // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
                     mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
                 tc::mma_commit(mbar);
@@ -714,7 +720,6 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     for (int i = 0; i < 16; ++i) {
                         dv[i] = __float2bfloat16(v[i] * __bfloat162float(gv[i]));
                         dz[i] = __bfloat162float(dv[i]);
-                        At[cmo(c0 + i, row, 128)] = dv[i];
                     }
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0, N_H)) = pack8(dv);
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0 + 8, N_H)) = pack8(dv + 8);

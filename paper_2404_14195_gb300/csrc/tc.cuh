@@ -2,9 +2,11 @@
 // the shared-memory barriers that track them, sm_100-family (sm_103a).
 //
 // Conventions used by the kernels here:
-//  * operands in shared memory in the no-swizzle, K-major "core matrix" layout:
-//    8 rows x 16 bytes (8 bf16) per core matrix; core matrices adjacent along K
-//    are LBO bytes apart, groups of 8 rows (M or N) are SBO bytes apart;
+//  * operands in shared memory in the no-swizzle "core matrix" layout: 8 rows x 16
+//    bytes (8 bf16) per core matrix; K-major: core matrices adjacent along K are
+//    LBO bytes apart, groups of 8 rows (M or N) SBO bytes apart; MN-major (rows
+//    along K, 8 consecutive M / N values per row): adjacent along M / N SBO apart,
+//    along K LBO apart;
 //  * accumulators in tensor memory (TMEM), allocated per CTA by one warp;
 //  * one thread issues tcgen05.mma and commits to an mbarrier; every waiter
 //    gives up after a wall-clock limit and reports an error instead of hanging.
@@ -110,6 +112,12 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// operand A / B read MN-major (the M / N index contiguous in each 16-byte core-matrix
+// row) instead of K-major.  For an MN-major no-swizzle operand, SBO is the byte
+// distance between core matrices adjacent along M / N and LBO the distance between
+// core matrices adjacent along K (checked against a host product of small integers).
+constexpr uint32_t IDESC_A_MN = 1u << 15, IDESC_B_MN = 1u << 16;
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
     asm volatile(
