@@ -405,7 +405,8 @@ __global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx,
 constexpr int FW_WBYTES = 2 * (N_H * N_IN + 3 * N_H * N_H + N_OUT_PAD * N_H);  // W_1..W_5
 constexpr int FB_WBYTES = 2 * (3 * N_H * N_H + N_H * N_OUT_PAD);               // W_2^T..W_5^T
 constexpr int TILE_BYTES = 2 * 128 * 128;
-constexpr size_t FW_SMEM = FW_WBYTES + TILE_BYTES + 64 + 1024;
+// forward: weights, one activation tile per tile group (NG groups of 256 threads)
+constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 64 + 1024; }
 constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 64 + 1024;
 
 struct FusedArgs {
@@ -434,6 +435,13 @@ __device__ __forceinline__ void smem_to_mma_sync() {
     __syncthreads();
     tc::fence_after_sync();
 }
+// the same over the 256 threads of tile group g (named barrier 1 + g)
+__device__ __forceinline__ void smem_to_mma_sync_group(int g) {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    asm volatile("bar.sync %0, 256;" ::"r"(1 + g) : "memory");
+    tc::fence_after_sync();
+}
 
 // D (TMEM) = A B^T over K, both operands K-major in shared memory (A: K_A = K columns)
 __device__ __forceinline__ void mma_chain(uint32_t d, const bf16 *A, const bf16 *Bm, int K, uint32_t idesc) {
@@ -448,21 +456,27 @@ __device__ __forceinline__ void mma_chain(uint32_t d, const bf16 *A, const bf16 
 // (widths wa, wb) in the K-major core layout above, read MN-major with K = the row
 // index.  Core matrices adjacent along K (8 rows) are 16 width bytes apart (LBO),
 // adjacent along M / N 128 bytes (SBO); one MMA takes 16 rows.
-__device__ __forceinline__ void mma_chain_rows(uint32_t d, const bf16 *A, int wa, const bf16 *Bm, int wb, uint32_t idesc) {
+// acc: add to the accumulator already in D instead of overwriting it.
+__device__ __forceinline__ void mma_chain_rows(uint32_t d, const bf16 *A, int wa, const bf16 *Bm, int wb, uint32_t idesc,
+                                               bool acc) {
     for (int kk = 0; kk < 8; ++kk) {
         const uint64_t da = tc::smem_desc(reinterpret_cast<const uint8_t *>(A) + kk * 32 * wa, 16 * wa, 128);
         const uint64_t db = tc::smem_desc(reinterpret_cast<const uint8_t *>(Bm) + kk * 32 * wb, 16 * wb, 128);
-        tc::mma_bf16(d, da, db, idesc | tc::IDESC_A_MN | tc::IDESC_B_MN, kk > 0 ? 1u : 0u);
+        tc::mma_bf16(d, da, db, idesc | tc::IDESC_A_MN | tc::IDESC_B_MN, (kk > 0 || acc) ? 1u : 0u);
     }
 }
 
 // 8 BF16 values as one 16-byte word
 __device__ __forceinline__ uint4 pack8(const bf16 *v) { return *reinterpret_cast<const uint4 *>(v); }
 
-// Both kernels run 256 threads: thread t serves row t % 128 of the tile (TMEM lane
-// t % 128, reachable by warps w and w + 4) and half h = t / 128 of each layer's
-// columns, so two warps per scheduler share the epilogue math.
-__global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
+// Both kernels run 256 threads per tile: thread t serves row t % 128 of the tile (TMEM
+// lane t % 128, reachable by warps w and w + 4) and half h = t / 128 of each layer's
+// columns, so two warps per scheduler share the epilogue math.  The forward kernel
+// runs NG such tile groups per CTA on the shared resident weights, each with its own
+// activation tile, TMEM columns, mbarrier and named barrier: while one group's
+// epilogue runs, the other's MMAs keep the tensor pipe busy.
+template <int NG>
+__global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
     extern __shared__ __align__(1024) uint8_t smem[];
     bf16 *sW[N_LAYERS];
     uint8_t *p = smem;
@@ -470,25 +484,26 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
         sW[l] = reinterpret_cast<bf16 *>(p);
         p += 2 * fan_out(l) * fan_in(l);
     }
-    bf16 *act = reinterpret_cast<bf16 *>(p);
-    p += TILE_BYTES;
-    uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
-    uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int row = t & 127, half = t >> 7;
+    const int grp = t >> 8, gt = t & 255;  // tile group, thread within it
+    const int row = gt & 127, half = gt >> 7;
+    bf16 *act = reinterpret_cast<bf16 *>(p + grp * TILE_BYTES);
+    p += NG * TILE_BYTES;
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1 + grp;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 1 + NG);
     if (warp == 0) {
-        tc::tmem_alloc(slot, 128);
+        tc::tmem_alloc(slot, 128 * NG);
         tc::tmem_relinquish();
     }
     if (t == 0) {
         tc::mbar_init(wbar, 1);
-        tc::mbar_init(mbar, 1);
+        for (int g = 0; g < NG; ++g) tc::mbar_init(wbar + 1 + g, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *slot, tlane = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t tmem = *slot + (uint32_t)(128 * grp), tlane = (uint32_t)((warp & 3) * 32) << 16;
     if (t == 0) {
         tc::mbar_arrive_expect_tx(wbar, FW_WBYTES);
         for (int l = 0; l < N_LAYERS; ++l) tc::bulk_copy_g2s(sW[l], f.Wc[l], 2 * fan_out(l) * fan_in(l), wbar);
@@ -496,7 +511,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
     bool ok = tc::mbar_wait(wbar, 0, WAIT_NS);
     uint32_t phase = 0;
     float lsum = 0.0f;
-    for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
+    for (int tile = blockIdx.x * NG + grp; ok && tile < (f.B >> 7); tile += gridDim.x * NG) {
         const int64_t r = (int64_t)tile * 128 + row;
         int64_t s;
         if (f.idx) s = f.idx[r];
@@ -543,8 +558,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
         for (int c = 0; c < N_OUT; ++c) tg[c] = half ? 0.0f : f.tgt[s * N_OUT + c];
         for (int l = 0; l < N_LAYERS && ok; ++l) {
             const int fi = fan_in(l), fo = fan_out(l);
-            smem_to_mma_sync();
-            if (t == 0) {
+            if (NG == 1) smem_to_mma_sync();
+            else smem_to_mma_sync_group(grp);
+            if (gt == 0) {
                 mma_chain(tmem, act, sW[l], fi, tc::idesc_bf16_f32(128, fo));
                 tc::mma_commit(mbar);
             }
@@ -594,14 +610,14 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fwd(FusedArgs f) {
         }
     }
     if (!ok) {  // a wait ran out: report, give the outstanding work one more bounded wait
-        if (t == 0) atomicExch(f.err, 1);
+        if (gt == 0) atomicExch(f.err, 1);
         tc::mbar_wait(mbar, phase, WAIT_NS);
     }
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
     if (lane == 0 && lsum != 0.0f) atomicAdd(f.loss, lsum);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (warp == 0) tc::tmem_dealloc(*slot, 128 * NG);
 }
 
 __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
@@ -621,8 +637,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int row = t & 127, half = t >> 7, wq = warp & 3;
+    // TMEM columns: 0..127 dH_{l-1} of the current layer (also dW_5^T and dW_1 of the
+    // current tile, read out at once); 128 l .. 128 l + 127 for l = 1, 2, 3: dW_{l+1}
+    // summed over all of this CTA's tiles, added into the gradient once at the end
     if (warp == 0) {
-        tc::tmem_alloc(slot, 256);
+        tc::tmem_alloc(slot, 512);
         tc::tmem_relinquish();
     }
     if (t == 0) {
@@ -634,6 +653,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot, tlane = (uint32_t)(wq * 32) << 16;
+    int ntiles = 0;  // tiles this CTA has finished
     if (t == 0) {
         tc::mbar_arrive_expect_tx(wbar, FB_WBYTES);
         for (int l = 1; l < N_LAYERS; ++l) tc::bulk_copy_g2s(sWt[l], f.Wtc[l], 2 * fan_out(l) * fan_in(l), wbar);
@@ -676,12 +696,36 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     *reinterpret_cast<uint4 *>(Hs + cmo(row, c, fi)) = reinterpret_cast<const uint4 *>(hin)[c >> 3];
             }
             smem_to_mma_sync();
-            if (t == 0) {
-                if (l == N_LAYERS - 1)  // dW_5^T [128 in][16 out] = H_4^T dZ_5
-                    mma_chain_rows(tmem + 128, Hs, fi, An, N_OUT_PAD, tc::idesc_bf16_f32(128, N_OUT_PAD));
-                else                    // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}
-                    mma_chain_rows(tmem + 128, An, fo, Hs, fi, tc::idesc_bf16_f32(128, fi));
-                if (l > 0)              // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
+            if (l == N_LAYERS - 1) {
+                // dW_5^T [128 in][16 out] = H_4^T dZ_5 into columns 0..15, read out (lane =
+                // input unit) before dH_4 takes those columns
+                if (t == 0) {
+                    mma_chain_rows(tmem, Hs, fi, An, N_OUT_PAD, tc::idesc_bf16_f32(128, N_OUT_PAD), false);
+                    tc::mma_commit(mbar);
+                }
+                ok = tc::mbar_wait(mbar, phase, WAIT_NS);
+                phase ^= 1;
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (half == 0) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + tlane, v);
+#pragma unroll
+                    for (int o = 0; o < N_OUT_PAD; ++o)
+                        if (v[o] != 0.0f) atomicAdd(f.grad + w_off_c(l) + o * N_H + row, v[o]);
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (t == 0) {  // dH_4 [128 rows][128] = dZ_5 W_5
+                    mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
+                    tc::mma_commit(mbar);
+                }
+            } else if (t == 0) {
+                // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}: the first layer's into columns
+                // 0..63 (no dH there), the others added to their per-CTA sums
+                mma_chain_rows(tmem + 128 * l, An, fo, Hs, fi, tc::idesc_bf16_f32(128, fi), l > 0 && ntiles > 0);
+                if (l > 0)  // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
                     mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
                 tc::mma_commit(mbar);
             }
@@ -689,19 +733,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             phase ^= 1;
             if (!ok) break;
             tc::fence_after_sync();
-            if (l == N_LAYERS - 1) {  // lane = input unit: dW_5[o][row], o < 16
-                if (half == 0) {
-                    float v[16];
-                    tc::tmem_ld16(tmem + tlane + 128, v);
-#pragma unroll
-                    for (int o = 0; o < N_OUT_PAD; ++o)
-                        if (v[o] != 0.0f) atomicAdd(f.grad + w_off_c(l) + o * N_H + row, v[o]);
-                }
-            } else {                  // lane = output unit: row `row` of dW_l, columns of this half
-                float *gw = f.grad + w_off_c(l) + (int64_t)row * fi;
+            if (l == 0) {  // lane = output unit: row `row` of dW_1, columns of this half
+                float *gw = f.grad + w_off_c(0) + (int64_t)row * fi;
                 for (int c0 = hw * half; c0 < hw * half + hw; c0 += 16) {
                     float v[16];
-                    tc::tmem_ld16(tmem + tlane + 128 + (uint32_t)c0, v);
+                    tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
 #pragma unroll
                     for (int i = 0; i < 16; i += 4) tc::red_add_v4(gw + c0 + i, v[i], v[i + 1], v[i + 2], v[i + 3]);
                 }
@@ -733,6 +769,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             }
             tc::fence_before_sync();
         }
+        ++ntiles;
+    }
+    if (ok && ntiles > 0) {  // this CTA's sums of dW_2 .. dW_4 (lane = output unit) into the gradient
+        tc::fence_after_sync();
+        for (int l = 1; l < N_LAYERS - 1; ++l) {
+            float *gw = f.grad + w_off_c(l) + (int64_t)row * N_H;
+            for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + tlane + (uint32_t)(128 * l + c0), v);
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) tc::red_add_v4(gw + c0 + i, v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+        }
     }
     if (!ok) {
         if (t == 0) atomicExch(f.err, 1);
@@ -740,11 +789,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 cudaError_t fused_set_smem() {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fw_smem(1));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fw_smem(2));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM);
     return e;
 }
@@ -948,8 +998,14 @@ cudaError_t enqueue_fused(rbf_mlp *mm, int B, uint64_t seed, const int64_t *expl
     f.dY = mm->dY.p; f.loss = mm->loss.p; f.grad = mm->grad.p;
     f.gscale = 2.0f / ((float)B * N_OUT);
     f.err = mm->errflag.p;
-    const unsigned grid = (unsigned)std::min(B / 128, std::max(mm->nsm, 1));
-    k_mlp_fwd<<<grid, 256, FW_SMEM, mm->st>>>(f);
+    // two tile groups per forward CTA once the tiles outnumber the SMs
+    const int tiles = B / 128, nsm = std::max(mm->nsm, 1);
+    const unsigned grid = (unsigned)std::min(tiles, nsm);
+    if (tiles > nsm) {
+        k_mlp_fwd<2><<<(unsigned)std::min((tiles + 1) / 2, nsm), 512, fw_smem(2), mm->st>>>(f);
+    } else {
+        k_mlp_fwd<1><<<grid, 256, fw_smem(1), mm->st>>>(f);
+    }
     k_mlp_bwd<<<grid, 256, FB_SMEM, mm->st>>>(f);
     mm->launches += 2;
     return cudaGetLastError();
