@@ -60,7 +60,8 @@ N_L, Q, DX, TAU_P, MAGIC = 30, 19, 0.004, 0.8, 3.0 / 16.0
 KERNELS = {0: "k_lbm_step<float,19> (256)", 1: "k_lbm_step_pairs<float,19,5>", 2: "k_lbm_step<float,19> (128)",
            3: "k_lbm_step_pairs<float,19,3>", 4: "k_lbm_step_pairs<float,19,6>", 5: "k_lbm_step_pairs<float,19,2>",
            6: "k_lbm_step_records<float,19,4> (256)", 7: "k_lbm_step_records<float,19,5> (256)",
-           8: "k_lbm_step_records<float,19,4> (128)", 9: "k_lbm_step_records<float,19,4> (64)"}
+           8: "k_lbm_step_records<float,19,4> (128)", 9: "k_lbm_step_records<float,19,4> (64)",
+           10: "k_lbm_step_records<float,19,4,PDL> (256)"}
 
 
 def workload():

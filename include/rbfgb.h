@@ -260,7 +260,9 @@ int rbf_profile_steps(rbf_ctx *ctx, int nsteps, double *kernel_ms, int *n_classe
  * to a multiple of 4 values, read with 16-byte loads: 6 one node per thread,
  * 256-thread blocks; 7 the same with registers capped so that five blocks fit
  * on an SM; 8 and 9 as 6 in blocks of 128 and 64 threads (finer blocks spread
- * the nodes more evenly over the SMs).  Switching between the two layouts on an initialised LBM
+ * the nodes more evenly over the SMs); 10 as 6, launched as a programmatic
+ * dependent launch (the next step's blocks are scheduled while this step drains
+ * and wait on the grid dependency before touching memory).  Switching between the two layouts on an initialised LBM
  * context rewrites the state (one kernel launch); the populations, as
  * rbf_lbm_get_populations reports them, are unchanged.
  * On a context whose weights were computed for RBF_SOLVER_ACM the code selects the
@@ -281,7 +283,7 @@ typedef struct {
 } rbf_tune_report;
 
 /* Autotuner: time every candidate schedule of the step kernels on this
- * context's own case (LBM: the ten fused-step schedules; ACM: the sweep codes
+ * context's own case (LBM: the eleven fused-step schedules; ACM: the sweep codes
  * 256, 128, 64, 2128, 2256, 4128, 4256 of rbf_set_kernel_variant), trial_steps steps each with CUDA events on
  * the context stream, keep the fastest.  The fields are saved before and restored
  * after the trials, so the state and step count are unchanged.  Needs rbf_init;

@@ -330,7 +330,7 @@ class Solver:
         block); 1 / 3 / 4 / 5 one population pair per warp, unrolled 5 / 3 / 6 / 2;
         6 / 7 one node per thread on the node-record layout (256 threads;
         registers capped for five blocks per SM); 8 / 9 as 6 with 128 / 64
-        threads per block.  The state is rewritten when the layout changes.
+        threads per block; 10 as 6 as a programmatic dependent launch.  The state is rewritten when the layout changes.
         ACM (after compute_weights for the ACM): threads per block (64, 128,
         256) + 1000 x lanes per node (2, 4; 0 for one) of the step sweeps."""
         self._ck(self._L.rbf_set_kernel_variant(self._h, int(variant)))

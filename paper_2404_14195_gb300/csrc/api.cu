@@ -891,7 +891,7 @@ int rbf_autotune(rbf_ctx *ctx, int trial_steps, rbf_tune_report *rep) {
     if (ctx->solver == RBF_SOLVER_LBM)
         cands = {LBM_PAIR_PER_WARP, LBM_NODE_PER_THREAD, LBM_NODE_PER_THREAD_128, LBM_PAIR_PER_WARP_U3,
                  LBM_PAIR_PER_WARP_U6, LBM_PAIR_PER_WARP_U2, LBM_RECORD_PER_THREAD, LBM_RECORD_PER_THREAD_OCC,
-                 LBM_RECORD_PER_THREAD_128, LBM_RECORD_PER_THREAD_64};
+                 LBM_RECORD_PER_THREAD_128, LBM_RECORD_PER_THREAD_64, LBM_RECORD_PER_THREAD_PDL};
     else
         cands = {256, 128, 64, 2128, 2256, 4128, 4256};
     rbf_tune_report r;

@@ -229,8 +229,11 @@ template <> struct Vec16<double> {
 // pairs layout).  MINB: blocks of 256 threads the compiler must fit on one SM,
 // i.e. a register cap (FP32: 4 -> 64 registers, no spills; 5 -> 48 registers, a
 // few spills, more warps in flight).  Same arithmetic, in the same order, as
-// k_lbm_step.
-template <typename T, int Q, int MINB, bool RA = false>
+// k_lbm_step.  PDL: launched as a programmatic dependent of the previous kernel in
+// the stream; every block first lets the next step's grid be scheduled, then waits
+// until the previous grid has completed and its writes are visible, before it
+// touches global memory.
+template <typename T, int Q, int MINB, bool RA = false, bool PDL = false>
 __global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
     using V = typename Vec2<T>::type;
     using W = Vec16<T>;
@@ -238,6 +241,10 @@ __global__ void __launch_bounds__(256, MINB) k_lbm_step_records(LbmArgs<T> a) {
     constexpr int NP = (Q - 1) / 2;
     constexpr int RL = lbm_rec_len(Q);
     constexpr int NV = RL / W::n;
+    if constexpr (PDL) {
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+    }
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int64_t s = i >> 5;
@@ -516,6 +523,20 @@ static cudaError_t launch_step_q(const LbmArgs<T> &a, cudaStream_t st, int code)
     case LBM_RECORD_PER_THREAD_64:
         k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2, RA><<<(unsigned)((a.n + 63) / 64), 64, 0, st>>>(a);
         break;
+    case LBM_RECORD_PER_THREAD_PDL: {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)((a.n + 255) / 256));
+        cfg.blockDim = dim3(256);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_lbm_step_records<T, Q, sizeof(T) == 4 ? 4 : 2, RA, true>, a);
+        if (e != cudaSuccess) return e;
+        break;
+    }
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

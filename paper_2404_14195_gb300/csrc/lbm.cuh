@@ -41,7 +41,10 @@ enum {
     LBM_RECORD_PER_THREAD = 6, LBM_RECORD_PER_THREAD_OCC = 7,
     // node layout, node per thread, 64-register kernel in blocks of 128 / 64 threads (finer
     // blocks spread the nodes more evenly over the SMs in a one-wave launch)
-    LBM_RECORD_PER_THREAD_128 = 8, LBM_RECORD_PER_THREAD_64 = 9, LBM_N_SCHEDULES = 10
+    LBM_RECORD_PER_THREAD_128 = 8, LBM_RECORD_PER_THREAD_64 = 9,
+    // as 6, launched as a programmatic dependent launch: the next step's blocks are
+    // scheduled while this step drains and wait on the hardware grid dependency
+    LBM_RECORD_PER_THREAD_PDL = 10, LBM_N_SCHEDULES = 11
 };
 __host__ __device__ constexpr int lbm_layout_of(int schedule) {
     return schedule >= LBM_RECORD_PER_THREAD ? LBM_LAYOUT_NODES : LBM_LAYOUT_PAIRS;

@@ -150,7 +150,8 @@ def _lbm_case(rbf, cell, q, prec, g_phys, n_l=25):
 
 
 @pytest.mark.parametrize("q,variant", [(19, 1), (15, 1), (19, 0), (15, 0), (19, 2), (19, 3), (19, 4), (15, 5),
-                                       (19, 6), (15, 6), (19, 7), (15, 7), (19, 8), (15, 9)])
+                                       (19, 6), (15, 6), (19, 7), (15, 7), (19, 8), (15, 9),
+                                       (19, 10), (15, 10)])
 def test_lbm_fp64_populations(rbf, cell, q, variant):
     # g large enough that f - omega is far above rounding (parity of the arithmetic)
     g = (2e4, 5e3, 0.0)
@@ -173,7 +174,7 @@ def test_lbm_fp64_populations(rbf, cell, q, variant):
     assert rel_inf(fields[:, 3], p_want) <= 1e-8
 
 
-@pytest.mark.parametrize("variant", [1, 0, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [1, 0, 6, 7, 8, 9, 10])
 def test_lbm_fp32_populations(rbf, cell, variant):
     q = 19
     g = (2e4, 5e3, 0.0)
@@ -190,7 +191,7 @@ def test_lbm_fp32_populations(rbf, cell, variant):
     assert rel_inf(got - om[:, None], want - om[:, None]) <= 1e-4
 
 
-@pytest.mark.parametrize("variant", [1, 0, 6, 7])
+@pytest.mark.parametrize("variant", [1, 0, 6, 7, 10])
 def test_lbm_fp32r_populations(rbf, cell, variant):
     """Refined FP32 (FP64 base + FP32 correction, one FP64 refresh every 64
     steps): after 200 steps (four refreshes) the populations follow the oracle
@@ -324,7 +325,7 @@ def test_autotune_keeps_state_and_parity(rbf, cell, orc_acm, solver):
         s.step(7)
         before = s.lbm_get_populations()
         times, chosen = s.autotune(10)
-        assert len(times) == 10 and chosen in times
+        assert len(times) == 11 and chosen in times
         assert np.array_equal(s.lbm_get_populations(), before)
         s.step(23)
         tm = oracle.tau_minus(0.8, 3.0 / 16.0)
