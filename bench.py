@@ -165,9 +165,8 @@ def kernel_traffic(kernel):
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "lbm_step_traffic.json")))
         src = open(os.path.join(ROOT, "paper_2404_14195_gb300", "csrc", "lbm.cu"), "rb").read()
-        if (rec.get("lbm_cu_sha256") == hashlib.sha256(src).hexdigest() and rec.get("nodes_full")
-                and rec.get("bench_kernel") == kernel):
-            return rec["dram_bytes_per_launch_full"]
+        if rec.get("lbm_cu_sha256") == hashlib.sha256(src).hexdigest() and rec.get("nodes_full"):
+            return rec["kernels"][kernel]["dram_bytes_per_launch_full"]
     except Exception:
         pass
     return None
