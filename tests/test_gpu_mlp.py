@@ -77,6 +77,33 @@ def test_gradient_matches_oracle(rbf):
         o += fo * fi + fo
 
 
+def test_gradient_matches_oracle_many_tiles(rbf):
+    """More 128-row tiles than SMs: the forward kernel runs two tile groups per CTA
+    and the backward kernel sums the hidden layers' weight gradients over each CTA's
+    tiles in tensor memory before reducing them.  Same bars as the small batch."""
+    m = rbf.Mlp(0)
+    theta = om.init_params(11).astype(np.float32).astype(np.float64)
+    m.set_params(theta)
+    xyz, r, sdf, X, T = _data(50000, seed=3)
+    m.set_data(xyz, r, sdf, T)
+    B = 128 * 321  # 321 tiles over at most 152 CTAs: uneven tile counts per group and per CTA
+    idx = (np.arange(B, dtype=np.int64) * 7919) % 50000
+    g, loss = m.gradient(idx)
+    th_b = theta.copy()
+    o = 0
+    for fo, fi in om.param_sizes():
+        th_b[o:o + fo * fi] = om.bf16_round(theta[o:o + fo * fi])
+        o += fo * fi + fo
+    loss_o, g_o = om.loss_and_grad(th_b, om.bf16_round(X[idx]), T[idx])
+    assert abs(loss - loss_o) <= 2e-2 * loss_o
+    o = 0
+    for li, (fo, fi) in enumerate(om.param_sizes()):
+        for sl in (slice(o, o + fo * fi), slice(o + fo * fi, o + fo * fi + fo)):
+            a, b = g[sl], g_o[sl]
+            assert np.abs(a - b).max() <= 3e-2 * np.abs(b).max() + 1e-12, (li, np.abs(a - b).max(), np.abs(b).max())
+        o += fo * fi + fo
+
+
 def test_adam_steps_match_oracle(rbf):
     m = rbf.Mlp(0)
     theta0 = om.init_params(11).astype(np.float32).astype(np.float64)
