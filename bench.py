@@ -367,6 +367,9 @@ def main():
             r = fn()
             blocks[name] = {k: r.get(k) for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step",
                                                  "dtype", "config", "roofline", "e2e", "gpu_launches", "clocks")}
+        if not args.no_cpu_baseline:  # after every timed region: bounded oracle samples
+            blocks["acm_config4"]["cpu_baseline"] = _cpu_sample_config4()
+            blocks["batch_config3"]["cpu_baseline"] = _cpu_sample_config3(cells3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tmax_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -604,7 +607,7 @@ def _acm_config4(args, rbf, local, dist, ws, peaks):
     }
 
 
-def _oracle_acm_baseline(case, c, budget_s=15.0):
+def _oracle_acm_baseline(case, c, budget_s=15.0, max_steps=100):
     import oracle
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -619,13 +622,35 @@ def _oracle_acm_baseline(case, c, budget_s=15.0):
     t0 = time.perf_counter()
     f, _ = oracle.acm_run(case, idx, w4, idxb, wgb, f, 1, dt=dt, v_ref=0.01)
     t1 = time.perf_counter() - t0
-    steps = int(max(1, min(100, budget_s / max(t1, 1e-6))))
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
     oracle.acm_run(case, idx, w4, idxb, wgb, f, steps, dt=dt, v_ref=0.01)
     dt_run = time.perf_counter() - t0
     return {"value": case.n * steps / dt_run, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} FP64 oracle ACM steps of the full {case.n}-node cell "
                       f"(stencils and weights untimed: {t_setup:.0f} s)"}
+
+
+def _cpu_sample_config4():
+    """Bounded CPU baseline for the config-4 block of the default line: the oracle
+    on a cell of the same family at a coarser resolution (the full cell's FP64
+    stencil and weight setup alone takes minutes on the host)."""
+    import synth
+    c = CFG4
+    small = synth.refined_cell(r=c["r"], h_min=0.02, h_max=0.03, ramp=0.32, seed=c["seed"])
+    b = _oracle_acm_baseline(small, c, budget_s=15.0, max_steps=5000)
+    b["sample"] = (f"config-4 family at h 0.02..0.03 (r={c['r']}, N_L={c['n_l']}, PHS r^{c['k']} + m={c['m']}): "
+                   + b["sample"].replace("of the full", "of a"))
+    return {k: b[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+
+def _cpu_sample_config3(cells):
+    """Bounded CPU baseline for the config-3 block: the oracle on the smallest of
+    the batch's cells, in node-steps/s."""
+    case, n_l = min(cells, key=lambda cn: cn[0].n)
+    b = _oracle_acm_baseline(case, dict(n_l=n_l, k=3, m=2), budget_s=15.0, max_steps=5000)
+    b["sample"] = f"the smallest of the {len(cells)} cells (N_L={n_l}): " + b["sample"].replace("of the full", "of its")
+    return {k: b[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
 
 def _batch_config3(args, rbf, local, dist, ws, peaks, cells):
