@@ -466,6 +466,32 @@ __device__ __forceinline__ void mma_chain_rows(uint32_t d, const bf16 *A, int wa
     }
 }
 
+// Column sums over a warp's 32 rows (lane = row) of the 16 values each lane holds:
+// a butterfly in which every step halves the values a lane carries (it keeps one
+// half, adds its partner's copy of that half and hands over the other), 8 + 4 + 2 +
+// 1 + 1 shuffles instead of 5 per value.  Returns the sum of column
+// col = 8 b4 + 4 b3 + 2 b2 + b1 (bK: bit K of the lane), held by lanes 2 col + {0, 1}.
+__device__ __forceinline__ float warp_colsum16(const float *v, int lane, int &col) {
+    float a[8], b[4], c[2];
+    bool hi = (lane & 16) != 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        a[i] = (hi ? v[i + 8] : v[i]) + __shfl_xor_sync(0xffffffffu, hi ? v[i] : v[i + 8], 16);
+    hi = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        b[i] = (hi ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, hi ? a[i] : a[i + 4], 8);
+    hi = (lane & 4) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        c[i] = (hi ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, hi ? b[i] : b[i + 2], 4);
+    hi = (lane & 2) != 0;
+    float d = (hi ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, hi ? c[0] : c[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    return d;
+}
+
 // 8 BF16 values as one 16-byte word
 __device__ __forceinline__ uint4 pack8(const bf16 *v) { return *reinterpret_cast<const uint4 *>(v); }
 
@@ -662,12 +688,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     uint32_t phase = 0;
     // column sums of this thread's dz values over its warp's 32 rows, into colsum[wq][c0 ..]
     auto colsum16 = [&](const float *dz, int c0) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            float sv = dz[i];
-            for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
-            if (lane == 0) colsum[wq * 128 + c0 + i] = sv;
-        }
+        int col;
+        const float sv = warp_colsum16(dz, lane, col);
+        if ((lane & 1) == 0) colsum[wq * 128 + c0 + col] = sv;
     };
     for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
         const int64_t r = (int64_t)tile * 128 + row;
