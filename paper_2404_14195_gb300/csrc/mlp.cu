@@ -407,7 +407,9 @@ constexpr int FB_WBYTES = 2 * (3 * N_H * N_H + N_H * N_OUT_PAD);               /
 constexpr int TILE_BYTES = 2 * 128 * 128;
 // forward: weights, one activation tile per tile group (NG groups of 256 threads)
 constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 64 + 1024; }
-constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 64 + 1024;
+// backward: W^T, the dZ and H tiles, column-sum scratch, per-CTA sums of db (5 x 128),
+// dW_5^T (16 x 128) and dW_1 (64 x 128) in FP32
+constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 4 * (5 * 128 + 16 * 128 + 64 * 128) + 64 + 1024;
 
 struct FusedArgs {
     int B;                       // rows, a multiple of 128
@@ -659,6 +661,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     p += 2 * TILE_BYTES;
     float *colsum = reinterpret_cast<float *>(p);             // [4 row groups][128 columns]
     p += 4 * 128 * 4;
+    // this CTA's sums over its tiles, each entry owned by one thread: db_l [l][column]
+    // (thread = column), dW_5^T [out][in] and dW_1 [in][out] (thread = the TMEM lane's unit)
+    float *dbsum = reinterpret_cast<float *>(p);
+    float *dw5 = dbsum + 5 * 128;
+    float *dw1 = dw5 + 16 * 128;
+    p += 4 * (5 * 128 + 16 * 128 + 64 * 128);
     uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
     uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -666,6 +674,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     // TMEM columns: 0..127 dH_{l-1} of the current layer (also dW_5^T and dW_1 of the
     // current tile, read out at once); 128 l .. 128 l + 127 for l = 1, 2, 3: dW_{l+1}
     // summed over all of this CTA's tiles, added into the gradient once at the end
+    for (int e = threadIdx.x; e < 5 * 128 + 16 * 128 + 64 * 128; e += blockDim.x) dbsum[e] = 0.0f;
     if (warp == 0) {
         tc::tmem_alloc(slot, 512);
         tc::tmem_relinquish();
@@ -707,10 +716,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             colsum16(dz, 0);
         }
         __syncthreads();
-        if (t < N_OUT_PAD) {
-            const float sv = colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
-            if (sv != 0.0f) atomicAdd(f.grad + b_off_c(N_LAYERS - 1) + t, sv);
-        }
+        if (t < N_OUT_PAD) dbsum[(N_LAYERS - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
         for (int l = N_LAYERS - 1; l >= 0 && ok; --l) {
             const int fi = fan_in(l), fo = fan_out(l), hw = fi >> 1;
             {   // the tile's rows of H_{l-1} (X for the first layer); half h: columns [h fi/2, (h+1) fi/2)
@@ -734,8 +740,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     float v[16];
                     tc::tmem_ld16(tmem + tlane, v);
 #pragma unroll
-                    for (int o = 0; o < N_OUT_PAD; ++o)
-                        if (v[o] != 0.0f) atomicAdd(f.grad + w_off_c(l) + o * N_H + row, v[o]);
+                    for (int o = 0; o < N_OUT_PAD; ++o) dw5[o * 128 + row] += v[o];
                 }
                 tc::fence_before_sync();
                 __syncthreads();
@@ -757,12 +762,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             if (!ok) break;
             tc::fence_after_sync();
             if (l == 0) {  // lane = output unit: row `row` of dW_1, columns of this half
-                float *gw = f.grad + w_off_c(0) + (int64_t)row * fi;
                 for (int c0 = hw * half; c0 < hw * half + hw; c0 += 16) {
                     float v[16];
                     tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
 #pragma unroll
-                    for (int i = 0; i < 16; i += 4) tc::red_add_v4(gw + c0 + i, v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    for (int i = 0; i < 16; ++i) dw1[(c0 + i) * 128 + row] += v[i];
                 }
             }
             if (l > 0) {  // dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1}); its column sums are db_{l-1}
@@ -785,16 +789,30 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     colsum16(dz, c0);
                 }
                 __syncthreads();
-                if (t < N_H) {
-                    const float sv = colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
-                    if (sv != 0.0f) atomicAdd(f.grad + b_off_c(l - 1) + t, sv);
-                }
+                if (t < N_H) dbsum[(l - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
             }
             tc::fence_before_sync();
         }
         ++ntiles;
     }
-    if (ok && ntiles > 0) {  // this CTA's sums of dW_2 .. dW_4 (lane = output unit) into the gradient
+    if (ok && ntiles > 0) {  // this CTA's sums into the gradient: dW_1, dW_5, db from shared memory,
+        // dW_2 .. dW_4 (lane = output unit) from TMEM
+        {
+            float *gw = f.grad + w_off_c(0) + (int64_t)row * N_IN;
+            for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 4)
+                tc::red_add_v4(gw + c0, dw1[c0 * 128 + row], dw1[(c0 + 1) * 128 + row], dw1[(c0 + 2) * 128 + row],
+                               dw1[(c0 + 3) * 128 + row]);
+            if (half == 0)
+                for (int o = 0; o < N_OUT_PAD; ++o) {
+                    const float v = dw5[o * 128 + row];
+                    if (v != 0.0f) atomicAdd(f.grad + w_off_c(N_LAYERS - 1) + o * N_H + row, v);
+                }
+            if (t < N_H)
+                for (int l = 0; l < N_LAYERS; ++l) {
+                    const float v = dbsum[l * 128 + t];
+                    if (v != 0.0f && (l < N_LAYERS - 1 || t < N_OUT_PAD)) atomicAdd(f.grad + b_off_c(l) + t, v);
+                }
+        }
         tc::fence_after_sync();
         for (int l = 1; l < N_LAYERS - 1; ++l) {
             float *gw = f.grad + w_off_c(l) + (int64_t)row * N_H;
