@@ -701,8 +701,32 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
         const float sv = warp_colsum16(dz, lane, col);
         if ((lane & 1) == 0) colsum[wq * 128 + c0 + col] = sv;
     };
+    // Global rows are loaded into registers while the MMAs run: this half's columns of the
+    // input of layer l (H_{l-1}, X for the first layer) for the next layer's staging, and of
+    // GELU'(Z_{l-1}) for this layer's epilogue.
+    uint4 hreg[8], greg[8];
+    auto load_h = [&](int l, int64_t rr) {
+        const int hw = fan_in(l) >> 1;
+        const uint4 *hin = reinterpret_cast<const uint4 *>(l > 0 ? f.H[l - 1] + rr * N_H : f.X + rr * N_IN);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < (hw >> 3)) hreg[k] = hin[((hw * half) >> 3) + k];
+    };
+    auto store_h = [&](int l) {
+        const int fi = fan_in(l), hw = fi >> 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < (hw >> 3)) *reinterpret_cast<uint4 *>(Hs + cmo(row, hw * half + 8 * k, fi)) = hreg[k];
+    };
+    auto load_g = [&](int l, int64_t rr) {
+        const uint4 *gr = reinterpret_cast<const uint4 *>(f.G[l - 1] + rr * N_H + 64 * half);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) greg[k] = gr[k];
+    };
+    if (blockIdx.x < (f.B >> 7)) load_h(N_LAYERS - 1, (int64_t)blockIdx.x * 128 + row);
     for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
         const int64_t r = (int64_t)tile * 128 + row;
+        const int64_t r_next = tile + (int)gridDim.x < (f.B >> 7) ? r + (int64_t)gridDim.x * 128 : -1;
         if (half == 0) {  // dZ_5 = dY (K = 16) and its column sums (db_5)
             __align__(16) bf16 dv[16];
             const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + r * N_OUT_PAD);
@@ -719,12 +743,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
         if (t < N_OUT_PAD) dbsum[(N_LAYERS - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
         for (int l = N_LAYERS - 1; l >= 0 && ok; --l) {
             const int fi = fan_in(l), fo = fan_out(l), hw = fi >> 1;
-            {   // the tile's rows of H_{l-1} (X for the first layer); half h: columns [h fi/2, (h+1) fi/2)
-                const bf16 *hin = l > 0 ? f.H[l - 1] + r * N_H : f.X + r * N_IN;
-                for (int c = hw * half; c < hw * half + hw; c += 8)
-                    *reinterpret_cast<uint4 *>(Hs + cmo(row, c, fi)) = reinterpret_cast<const uint4 *>(hin)[c >> 3];
-            }
+            store_h(l);  // the tile's rows of H_{l-1} (X for the first layer), this half's columns
             smem_to_mma_sync();
+            // the MMAs below no longer need the registers: fetch the next rows behind them
+            auto prefetch = [&]() {
+                if (l > 0) {
+                    load_g(l, r);
+                    load_h(l - 1, r);
+                } else if (r_next >= 0) {
+                    load_h(N_LAYERS - 1, r_next);
+                }
+            };
             if (l == N_LAYERS - 1) {
                 // dW_5^T [128 in][16 out] = H_4^T dZ_5 into columns 0..15, read out (lane =
                 // input unit) before dH_4 takes those columns
@@ -732,6 +761,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     mma_chain_rows(tmem, Hs, fi, An, N_OUT_PAD, tc::idesc_bf16_f32(128, N_OUT_PAD), false);
                     tc::mma_commit(mbar);
                 }
+                prefetch();
                 ok = tc::mbar_wait(mbar, phase, WAIT_NS);
                 phase ^= 1;
                 if (!ok) break;
@@ -749,13 +779,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
                     tc::mma_commit(mbar);
                 }
-            } else if (t == 0) {
-                // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}: the first layer's into columns
-                // 0..63 (no dH there), the others added to their per-CTA sums
-                mma_chain_rows(tmem + 128 * l, An, fo, Hs, fi, tc::idesc_bf16_f32(128, fi), l > 0 && ntiles > 0);
-                if (l > 0)  // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
-                    mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
-                tc::mma_commit(mbar);
+            } else {
+                if (t == 0) {
+                    // dW_l [128 out][fan_in] = dZ_l^T H_{l-1}: the first layer's into columns
+                    // 0..63 (no dH there), the others added to their per-CTA sums
+                    mma_chain_rows(tmem + 128 * l, An, fo, Hs, fi, tc::idesc_bf16_f32(128, fi), l > 0 && ntiles > 0);
+                    if (l > 0)  // dH_{l-1} [128 rows][fan_in] = dZ_l W_l
+                        mma_chain(tmem, An, sWt[l], fo, tc::idesc_bf16_f32(128, fi));
+                    tc::mma_commit(mbar);
+                }
+                prefetch();
             }
             ok = tc::mbar_wait(mbar, phase, WAIT_NS);
             phase ^= 1;
@@ -770,13 +803,14 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                 }
             }
             if (l > 0) {  // dZ_{l-1} = dH_{l-1} * GELU'(Z_{l-1}); its column sums are db_{l-1}
-                const bf16 *gr = f.G[l - 1] + r * N_H;
-                for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c0 = 64 * half + 16 * j;
                     float v[16];
                     tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
                     __align__(16) bf16 gv[16];
-                    *reinterpret_cast<uint4 *>(gv) = reinterpret_cast<const uint4 *>(gr + c0)[0];
-                    *reinterpret_cast<uint4 *>(gv + 8) = reinterpret_cast<const uint4 *>(gr + c0)[1];
+                    *reinterpret_cast<uint4 *>(gv) = greg[2 * j];
+                    *reinterpret_cast<uint4 *>(gv + 8) = greg[2 * j + 1];
                     __align__(16) bf16 dv[16];
                     float dz[16];
 #pragma unroll
