@@ -76,19 +76,41 @@ constexpr int SMEM_A = 16384, SMEM_B = 16384;
 constexpr size_t GEMM_SMEM = 57344;  // also caps residency at 3-4 CTAs per SM (<= 512 TMEM columns)
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
+// GELU in its tanh form, h = z (1 + tanh u) / 2 with u = sqrt(2/pi) (z + 0.044715 z^3),
+// evaluated through the identity (1 + tanh u) / 2 = s = 1 / (1 + 2^a), a = -2u log2(e):
+// one hardware base-2 exponential and one hardware reciprocal (PTX ex2.approx and
+// rcp.approx, a few ulp; ~1e-6 against the tanh form, far below the BF16 resolution h is
+// stored at) instead of a full-precision tanhf.  The derivative follows from
+// 1 - tanh^2 u = 4 s (1 - s):
+//   h' = s + 2 z s (1 - s) u' = s + h (1 - s) 2u',  2u' = 2 sqrt(2/pi) (1 + 3 * 0.044715 z^2).
+// a is clamped at 126 so that 1 + 2^a stays finite (s >= 2^-126 there instead of ~0).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// GELU h and its derivative g from one exponential
+__device__ __forceinline__ void gelu_both(float z, float &h, float &g) {
+    const float zz = z * z;
+    const float a = fminf(z * fmaf(0.044715f, zz, 1.0f) * -2.302208198144325f, 126.0f);
+    const float s = rcp_approx(1.0f + ex2_approx(a));
+    h = z * s;
+    g = fmaf(h * (1.0f - s), fmaf(0.21406444881780073f, zz, 1.5957691216057308f), s);
+}
 __device__ __forceinline__ float gelu_f(float z) {
-    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
-    return 0.5f * z * (1.0f + t);
+    float h, g;
+    gelu_both(z, h, g);
+    return h;
 }
 __device__ __forceinline__ float gelu_prime_f(float z) {
-    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
-    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
-}
-// GELU and its derivative from one tanh (same expressions as gelu_f, gelu_prime_f)
-__device__ __forceinline__ void gelu_both(float z, float &h, float &g) {
-    const float t = tanhf(0.7978845608028654f * (z + 0.044715f * z * z * z));
-    h = 0.5f * z * (1.0f + t);
-    g = 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
+    float h, g;
+    gelu_both(z, h, g);
+    return g;
 }
 
 // copy rows [r0, r0 + nrows) x cols [k0, k0 + kw) of a K-major BF16 matrix into the
@@ -179,8 +201,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
                 float h, gp = 0.0f;
                 if (EP == EP_FWD) {
                     const float z = v[i] + g.bias[c];
-                    h = gelu_f(z);
-                    gp = gelu_prime_f(z);
+                    gelu_both(z, h, gp);
                 } else if (EP == EP_OUT) {
                     const float y = v[i] + g.bias[c];
                     float dy = 0.0f;
@@ -405,8 +426,10 @@ __global__ void k_node_geo(int64_t n, const double *__restrict__ xyz, double cx,
 constexpr int FW_WBYTES = 2 * (N_H * N_IN + 3 * N_H * N_H + N_OUT_PAD * N_H);  // W_1..W_5
 constexpr int FB_WBYTES = 2 * (3 * N_H * N_H + N_H * N_OUT_PAD);               // W_2^T..W_5^T
 constexpr int TILE_BYTES = 2 * 128 * 128;
-// forward: weights, one activation tile per tile group (NG groups of 256 threads)
-constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 64 + 1024; }
+// all five layers' biases, layer l at [128 l, 128 l + fan_out(l))
+constexpr int FW_NBIAS = 4 * 128 + N_OUT_PAD;
+// forward: weights, one activation tile per tile group (NG groups of 256 threads), biases
+constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 4 * FW_NBIAS + 64 + 1024; }
 // backward: W^T, the dZ and H tiles, column-sum scratch, per-CTA sums of db (5 x 128),
 // dW_5^T (16 x 128) and dW_1 (64 x 128) in FP32
 constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 4 * (5 * 128 + 16 * 128 + 64 * 128) + 64 + 1024;
@@ -517,6 +540,8 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
     const int row = gt & 127, half = gt >> 7;
     bf16 *act = reinterpret_cast<bf16 *>(p + grp * TILE_BYTES);
     p += NG * TILE_BYTES;
+    float *sB = reinterpret_cast<float *>(p);  // the biases (FP32 masters), read by every epilogue
+    p += 4 * FW_NBIAS;
     uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1 + grp;
     uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 1 + NG);
     if (warp == 0) {
@@ -527,6 +552,10 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
         tc::mbar_init(wbar, 1);
         for (int g = 0; g < NG; ++g) tc::mbar_init(wbar + 1 + g, 1);
         tc::fence_mbar_init();
+    }
+    for (int i = t; i < FW_NBIAS; i += blockDim.x) {
+        const int l = i >> 7, c = i & 127;
+        sB[i] = f.theta[b_off_c(l) + c];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -596,20 +625,27 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
             phase ^= 1;
             if (!ok) break;
             tc::fence_after_sync();
-            const float *bias = f.theta + b_off_c(l);
+            const float *bias = sB + 128 * l;
             if (l < N_LAYERS - 1) {
                 for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
                     float v[16];
                     tc::tmem_ld16(tmem + tlane + (uint32_t)c0, v);
-                    __align__(16) bf16 hv[16];
-                    __align__(16) bf16 gv[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        float h, g;
-                        gelu_both(v[i] + bias[c0 + i], h, g);
-                        hv[i] = __float2bfloat16(h);
-                        gv[i] = __float2bfloat16(g);
+                    for (int k = 0; k < 4; ++k) {  // z = accumulator + bias, the bias as four 16-byte loads
+                        const float4 q = reinterpret_cast<const float4 *>(bias + c0)[k];
+                        v[4 * k] += q.x; v[4 * k + 1] += q.y; v[4 * k + 2] += q.z; v[4 * k + 3] += q.w;
                     }
+                    __align__(16) __nv_bfloat162 hv2[8];
+                    __align__(16) __nv_bfloat162 gv2[8];
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {  // pairs: one two-value conversion each
+                        float h0, g0, h1, g1;
+                        gelu_both(v[i], h0, g0);
+                        gelu_both(v[i + 1], h1, g1);
+                        hv2[i >> 1] = __floats2bfloat162_rn(h0, h1);
+                        gv2[i >> 1] = __floats2bfloat162_rn(g0, g1);
+                    }
+                    const bf16 *hv = reinterpret_cast<const bf16 *>(hv2), *gv = reinterpret_cast<const bf16 *>(gv2);
                     *reinterpret_cast<uint4 *>(act + cmo(row, c0, N_H)) = pack8(hv);
                     *reinterpret_cast<uint4 *>(act + cmo(row, c0 + 8, N_H)) = pack8(hv + 8);
                     uint4 *hd = reinterpret_cast<uint4 *>(f.H[l] + r * N_H + c0);
@@ -723,15 +759,25 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) greg[k] = gr[k];
     };
-    if (blockIdx.x < (f.B >> 7)) load_h(N_LAYERS - 1, (int64_t)blockIdx.x * 128 + row);
+    uint4 dyreg[2];  // the tile's output error row dY (half 0), fetched with the tile's H_4 rows
+    auto load_dy = [&](int64_t rr) {
+        if (half == 0) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + rr * N_OUT_PAD);
+            dyreg[0] = src[0];
+            dyreg[1] = src[1];
+        }
+    };
+    if (blockIdx.x < (f.B >> 7)) {
+        load_h(N_LAYERS - 1, (int64_t)blockIdx.x * 128 + row);
+        load_dy((int64_t)blockIdx.x * 128 + row);
+    }
     for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
         const int64_t r = (int64_t)tile * 128 + row;
         const int64_t r_next = tile + (int)gridDim.x < (f.B >> 7) ? r + (int64_t)gridDim.x * 128 : -1;
         if (half == 0) {  // dZ_5 = dY (K = 16) and its column sums (db_5)
             __align__(16) bf16 dv[16];
-            const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + r * N_OUT_PAD);
-            *reinterpret_cast<uint4 *>(dv) = src[0];
-            *reinterpret_cast<uint4 *>(dv + 8) = src[1];
+            *reinterpret_cast<uint4 *>(dv) = dyreg[0];
+            *reinterpret_cast<uint4 *>(dv + 8) = dyreg[1];
             *reinterpret_cast<uint4 *>(An + cmo(row, 0, N_OUT_PAD)) = pack8(dv);
             *reinterpret_cast<uint4 *>(An + cmo(row, 8, N_OUT_PAD)) = pack8(dv + 8);
             float dz[16];
@@ -752,6 +798,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     load_h(l - 1, r);
                 } else if (r_next >= 0) {
                     load_h(N_LAYERS - 1, r_next);
+                    load_dy(r_next);
                 }
             };
             if (l == N_LAYERS - 1) {
@@ -811,13 +858,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     __align__(16) bf16 gv[16];
                     *reinterpret_cast<uint4 *>(gv) = greg[2 * j];
                     *reinterpret_cast<uint4 *>(gv + 8) = greg[2 * j + 1];
-                    __align__(16) bf16 dv[16];
+                    __align__(16) __nv_bfloat162 dv2[8];
                     float dz[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        dv[i] = __float2bfloat16(v[i] * __bfloat162float(gv[i]));
-                        dz[i] = __bfloat162float(dv[i]);
+                    for (int i = 0; i < 16; i += 2) {  // pairs: one two-value conversion each
+                        const float2 gf = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(gv)[i >> 1]);
+                        dv2[i >> 1] = __floats2bfloat162_rn(v[i] * gf.x, v[i + 1] * gf.y);
+                        const float2 df = __bfloat1622float2(dv2[i >> 1]);
+                        dz[i] = df.x;
+                        dz[i + 1] = df.y;
                     }
+                    const bf16 *dv = reinterpret_cast<const bf16 *>(dv2);
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0, N_H)) = pack8(dv);
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0 + 8, N_H)) = pack8(dv + 8);
                     colsum16(dz, c0);
