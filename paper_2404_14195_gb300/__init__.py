@@ -158,6 +158,18 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _out(out, shape):
+    """A float64 array of ``shape`` to receive a result: a new one, or the caller's
+    ``out`` written in place (for instance a pinned host buffer, which the library's
+    device-to-host copy then writes directly)."""
+    if out is None:
+        return np.empty(shape, np.float64)
+    if (not isinstance(out, np.ndarray) or out.dtype != np.float64 or out.shape != tuple(shape)
+            or not out.flags.c_contiguous or not out.flags.writeable):
+        raise ValueError(f"out must be a writeable C-contiguous float64 array of shape {tuple(shape)}")
+    return out
+
+
 class Solver:
     """One case on one GPU: nodes, stencils, weights, fields (an ``rbf_ctx``)."""
 
@@ -250,8 +262,8 @@ class Solver:
     def step(self, nsteps: int):
         self._ck(self._L.rbf_step(self._h, int(nsteps)))
 
-    def get_fields(self):
-        out = np.empty((self.n, 4), np.float64)
+    def get_fields(self, out=None):
+        out = _out(out, (self.n, 4))
         self._ck(self._L.rbf_get_fields(self._h, _ptr(out)))
         return out
 
@@ -260,8 +272,8 @@ class Solver:
         assert a.shape == (self.n, 4)
         self._ck(self._L.rbf_set_fields(self._h, _ptr(a)))
 
-    def lbm_get_populations(self):
-        out = np.empty((self.q, self.n), np.float64)
+    def lbm_get_populations(self, out=None):
+        out = _out(out, (self.q, self.n))
         self._ck(self._L.rbf_lbm_get_populations(self._h, _ptr(out)))
         return out
 

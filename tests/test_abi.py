@@ -60,3 +60,23 @@ def test_header_compiles_for_c_and_cpp_callers(tmp_path, compiler, std, ext):
     r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_output_buffers_are_checked_before_any_call():
+    """Result readers write a caller's buffer in place (a pinned host array, so the
+    device-to-host copy lands there directly) only when it has the result's shape,
+    float64 type and C layout; anything else is refused before the C ABI is called."""
+    import numpy as np
+
+    from paper_2404_14195_gb300 import _out
+    a = _out(None, (5, 4))
+    assert a.shape == (5, 4) and a.dtype == np.float64
+    b = np.zeros((5, 4))
+    assert _out(b, (5, 4)) is b
+    for bad in (np.zeros((4, 5)), np.zeros((5, 4), np.float32), np.zeros((5, 8))[:, ::2], [[0.0] * 4] * 5):
+        with pytest.raises(ValueError):
+            _out(bad, (5, 4))
+    ro = np.zeros((5, 4))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        _out(ro, (5, 4))
