@@ -31,14 +31,14 @@ import synth  # noqa: E402
 OUT = os.path.join(HERE, "steady_references.json")
 
 
-def _mns(case, n_l, v_ref, m_p, window, tol, max_steps):
+def _mns(case, n_l, v_ref, m_p, window, tol, max_steps, k=3, m=2):
     idx = oracle.knn(case["xyz"], case["xyz"], n_l, grid=case.n > 20000 or None)
-    w4 = oracle.acm_weights(case["xyz"], idx)
+    w4 = oracle.acm_weights(case["xyz"], idx, k, m)
     wl, idxb = oracle.neumann_stencils(case, n_l)
-    wgb = oracle.neumann_weights(case, idxb)
+    wgb = oracle.neumann_weights(case, idxb, k, m)
     h_min = np.linalg.norm(oracle.min_image(case["xyz"][idx[:, 1]] - case["xyz"]), axis=1).min()
     dt = oracle.acm_dt(h_min, 1.0)
-    pr = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], m_p, n_l)
+    pr = oracle.probe_setup(case["xyz"], case["centre"], case["radius"], m_p, n_l, k, m)
     f = np.zeros((case.n, 4))
     steps, prev = 0, None
     while True:
@@ -112,6 +112,14 @@ for _i, _r in enumerate(HELDOUT_RADII):
     ENTRIES[f"mns_c5_heldout_{_i}"] = dict(
         case=dict(kind="jittered", r=_r, n_axis=40, seed=900 + _i),
         run=lambda c: _mns(c, 25, 2.0, 32, 4000, 1e-8, 400000))
+
+# The family of the large mixed-precision ACM cell (r = 0.45, PHS r^5 + order-3
+# monomials, N_L = 40) at a resolution the oracle can take to its steady state
+# (h 0.02 at the wall to 0.03, 52,941 nodes; the 3M-node cell at h 0.003..0.02
+# needs ~1e6 steps), MNS at v_ref = 2.
+ENTRIES["mns_config4_family"] = dict(
+    case=dict(kind="refined", r=0.45, h_min=0.02, h_max=0.03, ramp=0.32, seed=4),
+    run=lambda c: _mns(c, 40, 2.0, 32, 4000, 1e-8, 400000, k=5, m=3))
 
 
 def make_case(spec):
