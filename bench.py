@@ -33,6 +33,8 @@ Other workloads (--workload), same line format:
   batch-config3  64 cells stepped in one persistent launch
   mlp-train      warm-start network training steps (fused tensor-core kernels)
   tts-config1    the time-to-steady block alone
+  tts-config4-family  its config-4-family arms alone (FP64, compensated and plain FP32
+                 to residual 1e-7 on a 52,941-node cell, against the oracle)
   warmstart-config5  the learned warm start at the configured node counts: the
                  network trained on steady fields of --cells cells (h = 1/40,
                  41k-58k nodes) and evaluated on five held-out radii against the
@@ -220,6 +222,9 @@ def run_reference(args):
     return 0
 
 
+SUB_STEPS = 2000  # timed steps of each extra workload block of the default line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -232,7 +237,7 @@ def main():
                     help="LBM step schedule (rbf_set_kernel_variant code); -1 = autotune on the case")
     ap.add_argument("--workload", default="lbm-config2",
                     choices=["lbm-config2", "acm-config4", "batch-config3", "mlp-train", "tts-config1",
-                             "warmstart-config5"],
+                             "tts-config4-family", "warmstart-config5"],
                     help="lbm-config2 (default, the headline); acm-config4: ~3M-node ACM cell, r^5, m=3, N_L=40, "
                          "FP32; batch-config3: 64-cell porosity sweep in one persistent launch; mlp-train: "
                          "warm-start network training steps on the tensor cores")
@@ -356,11 +361,15 @@ def main():
     tts = None
     if not args.no_tts and ws == 1:
         tts = {"acm_config1": _tts_acm_config1(rbf, local, refs.get("mns_config1_vref2")),
-               "mlbm_config2": _tts_mlbm_config2(rbf, local, case, refs.get("mlbm_config2"))}
+               "mlbm_config2": _tts_mlbm_config2(rbf, local, case, refs.get("mlbm_config2")),
+               "acm_config4_family": _tts_acm_config4_family(rbf, local, refs.get("mns_config4_family"))}
     blocks = None
     if not args.no_workloads and ws == 1:
         sub = argparse.Namespace(**vars(args))
         sub.no_cpu_baseline, sub.e2e_steps = True, 10
+        # at most SUB_STEPS timed steps per block (5.3 s of config-4 steps, 11.6 s of config-3
+        # steps), so the default line stays within a few minutes at the headline's K = 20,000
+        sub.steps = min(args.steps, SUB_STEPS)
         blocks = {}
         for name, fn in (("acm_config4", lambda: _acm_config4(sub, rbf, local, None, 1, peaks)),
                          ("batch_config3", lambda: _batch_config3(sub, rbf, local, None, 1, peaks, cells3))):
@@ -496,6 +505,8 @@ def run_workload(args):
         line = _batch_config3(args, rbf, local, dist, ws, peaks, cells3)
     elif args.workload == "tts-config1":
         line = _tts_config1(args, rbf, local)
+    elif args.workload == "tts-config4-family":
+        line = _tts_config4_family(args, rbf, local)
     elif args.workload == "warmstart-config5":
         line = _warmstart_config5(args, rbf, local)
     else:
@@ -787,6 +798,17 @@ def _tts_config1(args, rbf, local):
             "tts": {"acm_config1": acm, "mlbm_config2": lbm}}
 
 
+def _tts_config4_family(args, rbf, local):
+    """The config-4-family arms of the time-to-steady block on their own, as one
+    JSON line whose value is the compensated FP32 run's seconds to residual 1e-7."""
+    blk = _tts_acm_config4_family(rbf, local, golden_references().get("mns_config4_family"))
+    at = blk.get("runs", {}).get("fp32c", {}).get("at_residual") or {}
+    return {"metric": "time to residual 1e-7 (config 4 family), error against the FP64 GPU path and the oracle",
+            "value": at.get("seconds"), "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 compensated", "data": "synthetic (seeded cell)",
+            "config": {"workload": blk.get("workload")}, "tts": {"acm_config4_family": blk}}
+
+
 def golden_references():
     """The FP64 oracle's steady k/d^2 and K on the time-to-steady cells, written by
     tests/golden/make_steady_references.py (oracle only, run once on the CPU)."""
@@ -851,6 +873,74 @@ def _tts_acm_config1(rbf, local, ref, chunk=500, max_steps=24000, m_p=32, v_ref=
                         "train_cells_converged": sum(r["status"] == 0 for r in res3), "train_s": t_train,
                         "final_train_loss": float(hist[-1])},
             "clocks": clk.summary()}
+
+
+CFG4_FAMILY = dict(r=0.45, h_min=0.02, h_max=0.03, ramp=0.32, seed=4)  # 52,941 nodes
+
+
+def _tts_acm_config4_family(rbf, local, ref, chunk=2000, max_steps=40000, m_p=32, v_ref=2.0, res_tol=1e-7):
+    """Config 4's report (run to residual 1e-7; error against the FP64 GPU path and
+    the oracle on a 1e-4 permeability target) on a cell of its family that the
+    oracle can take to its steady state: r = 0.45, PHS r^5 + order-3 monomials,
+    N_L = 40, h 0.02 at the wall to 0.03 (52,941 nodes; the 3.0M-node cell at h
+    0.003..0.02 would need ~1e6 steps), v_ref = 2.  FP64, compensated FP32 and
+    plain FP32 from rest through the persistent driver (schedule tuned per
+    precision), in chunks; after each chunk the residual of the last step, k/d^2 and
+    K.  Per run: the first chunk whose residual is below res_tol (steps, seconds, k
+    and K errors there), and the first chunk after which k stays within 1e-4 of the
+    oracle's k (time to steady); seconds count the stepping, not the reads."""
+    import synth
+    case = synth.refined_cell(**CFG4_FAMILY)
+    if not ref or ref.get("nodes") != case.n:
+        return {"unavailable": "no oracle reference for this cell in tests/golden/steady_references.json"}
+    k_ref, K_ref = ref["k_over_d2"], ref["K"]
+    clk = Clocks(local)
+    clk.__enter__()
+    runs = {}
+    for name, prec in (("fp64", rbf.RBF_FP64), ("fp32c", rbf.RBF_FP32C), ("fp32", rbf.RBF_FP32)):
+        s = rbf.Solver(local)
+        s.set_case(case)
+        s.build_stencils(CFG4["n_l"])
+        s.compute_weights(k=CFG4["k"], m=CFG4["m"], solver=rbf.RBF_SOLVER_ACM)
+        s.init(precision=prec, v_ref=v_ref)
+        code = s.autotune_persistent(500)[1]
+        hist, t_run, steps = [], 0.0, 0
+        while steps < max_steps:
+            t1 = time.perf_counter()
+            r = s.solve(chunk, 1e-300, check_every=chunk, m_p=m_p)
+            t_run += time.perf_counter() - t1
+            steps += chunk
+            k = s.permeability(m_p)[0]
+            K = s.drag(m_p)[1]
+            hist.append((steps, k, t_run, r["residual"], K))
+        s.close()
+        hit = _first_within(hist, k_ref)
+        at = next((h for h in hist if h[3] <= res_tol), None)
+        runs[name] = {
+            "persistent_schedule": code, "s_per_step": hist[-1][2] / hist[-1][0],
+            "residual_end": hist[-1][3],
+            "at_residual": None if at is None else {
+                "steps": at[0], "seconds": at[2], "residual": at[3],
+                "k_rel_err_vs_oracle": abs(at[1] - k_ref) / k_ref, "K_rel_err_vs_oracle": abs(at[4] - K_ref) / K_ref,
+                "k": at[1], "K": at[4]},
+            "to_1e-4_of_oracle_k": None if hit is None else {"steps": hit[0], "seconds": hit[2]},
+            "k_end_rel_err_vs_oracle": abs(hist[-1][1] - k_ref) / k_ref,
+            "K_end_rel_err_vs_oracle": abs(hist[-1][4] - K_ref) / K_ref,
+            "k_end": hist[-1][1], "K_end": hist[-1][4]}
+    clk.__exit__(None, None, None)
+    base = runs["fp64"]
+    for v in runs.values():
+        a, b = v["at_residual"], base["at_residual"]
+        if a and b:
+            a["k_rel_err_vs_gpu_fp64"] = abs(a["k"] - b["k"]) / abs(b["k"])
+            a["K_rel_err_vs_gpu_fp64"] = abs(a["K"] - b["K"]) / abs(b["K"])
+        t, t0 = v["to_1e-4_of_oracle_k"], base["to_1e-4_of_oracle_k"]
+        v["speedup_vs_fp64"] = (t0["seconds"] / t["seconds"]) if (t and t0) else None
+    return {"workload": f"config-4 family MNS cell ({case.n} nodes, r=0.45, h 0.02..0.03, N_L={CFG4['n_l']}, "
+                        f"PHS r^{CFG4['k']} + m={CFG4['m']}), v_ref={v_ref}, chunks of {chunk} steps up to {max_steps}",
+            "k_ref": k_ref, "K_ref": K_ref,
+            "ref_source": f"FP64 oracle, {ref['steps']} steps (tests/golden/steady_references.json)",
+            "residual_criterion": res_tol, "runs": runs, "clocks": clk.summary()}
 
 
 def _tts_mlbm_config2(rbf, local, case, ref, chunk=5000, max_steps=250000, m_p=32):
