@@ -434,6 +434,12 @@ constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 4 * FW_N
 // dW_5^T (16 x 128) and dW_1 (64 x 128) in FP32
 constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 4 * (5 * 128 + 16 * 128 + 64 * 128) + 64 + 1024;
 
+// H_l and GELU'(Z_l) between the fused forward and backward kernels (private to
+// them): per 128-row tile, 16 chunks of 8 columns, each chunk's 128 rows contiguous at
+// 16 bytes per row, so the 32 lanes of a warp (32 consecutive rows of the tile) write
+// or read 512 contiguous bytes per 16-byte access.  Element offset of chunk q of row r.
+__device__ __forceinline__ int64_t hg_off(int64_t r, int q) { return (((r >> 7) * 16 + q) * 128 + (r & 127)) * 8; }
+
 struct FusedArgs {
     int B;                       // rows, a multiple of 128
     int64_t n;                   // samples in the data
@@ -446,7 +452,7 @@ struct FusedArgs {
     const bf16 *Wtc[N_LAYERS];   // W_l^T [fan_in][fan_out], core layout, K = fan_out (l >= 1)
     const float *theta;          // FP32 masters (biases)
     bf16 *X;                     // [B][64]
-    bf16 *H[4], *G[4];           // [B][128]
+    bf16 *H[4], *G[4];           // B x 128 in the chunked layout of hg_off
     bf16 *dY;                    // [B][16]
     float *loss, *grad;
     float gscale;
@@ -648,10 +654,11 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
                     const bf16 *hv = reinterpret_cast<const bf16 *>(hv2), *gv = reinterpret_cast<const bf16 *>(gv2);
                     *reinterpret_cast<uint4 *>(act + cmo(row, c0, N_H)) = pack8(hv);
                     *reinterpret_cast<uint4 *>(act + cmo(row, c0 + 8, N_H)) = pack8(hv + 8);
-                    uint4 *hd = reinterpret_cast<uint4 *>(f.H[l] + r * N_H + c0);
-                    uint4 *gd = reinterpret_cast<uint4 *>(f.G[l] + r * N_H + c0);
-                    hd[0] = pack8(hv); hd[1] = pack8(hv + 8);
-                    gd[0] = pack8(gv); gd[1] = pack8(gv + 8);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        *reinterpret_cast<uint4 *>(f.H[l] + hg_off(r, (c0 >> 3) + k)) = pack8(hv + 8 * k);
+                        *reinterpret_cast<uint4 *>(f.G[l] + hg_off(r, (c0 >> 3) + k)) = pack8(gv + 8 * k);
+                    }
                 }
             } else if (half == 0) {
                 float v[16];
@@ -743,10 +750,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     uint4 hreg[8], greg[8];
     auto load_h = [&](int l, int64_t rr) {
         const int hw = fan_in(l) >> 1;
-        const uint4 *hin = reinterpret_cast<const uint4 *>(l > 0 ? f.H[l - 1] + rr * N_H : f.X + rr * N_IN);
+        if (l > 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (k < (hw >> 3)) hreg[k] = hin[((hw * half) >> 3) + k];
+            for (int k = 0; k < 8; ++k)
+                hreg[k] = *reinterpret_cast<const uint4 *>(f.H[l - 1] + hg_off(rr, ((hw * half) >> 3) + k));
+        } else {  // X [B][64], row-major
+            const uint4 *hin = reinterpret_cast<const uint4 *>(f.X + rr * N_IN);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hreg[k] = hin[((hw * half) >> 3) + k];
+        }
     };
     auto store_h = [&](int l) {
         const int fi = fan_in(l), hw = fi >> 1;
@@ -755,9 +767,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             if (k < (hw >> 3)) *reinterpret_cast<uint4 *>(Hs + cmo(row, hw * half + 8 * k, fi)) = hreg[k];
     };
     auto load_g = [&](int l, int64_t rr) {
-        const uint4 *gr = reinterpret_cast<const uint4 *>(f.G[l - 1] + rr * N_H + 64 * half);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) greg[k] = gr[k];
+        for (int k = 0; k < 8; ++k) greg[k] = *reinterpret_cast<const uint4 *>(f.G[l - 1] + hg_off(rr, 8 * half + k));
     };
     uint4 dyreg[2];  // the tile's output error row dY (half 0), fetched with the tile's H_4 rows
     auto load_dy = [&](int64_t rr) {
