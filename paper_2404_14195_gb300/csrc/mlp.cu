@@ -434,11 +434,16 @@ constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 4 * FW_N
 // dW_5^T (16 x 128) and dW_1 (64 x 128) in FP32
 constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 4 * (5 * 128 + 16 * 128 + 64 * 128) + 64 + 1024;
 
-// H_l and GELU'(Z_l) between the fused forward and backward kernels (private to
-// them): per 128-row tile, 16 chunks of 8 columns, each chunk's 128 rows contiguous at
-// 16 bytes per row, so the 32 lanes of a warp (32 consecutive rows of the tile) write
-// or read 512 contiguous bytes per 16-byte access.  Element offset of chunk q of row r.
-__device__ __forceinline__ int64_t hg_off(int64_t r, int q) { return (((r >> 7) * 16 + q) * 128 + (r & 127)) * 8; }
+// The features X, H_l, GELU'(Z_l) and the output error dY between the fused forward
+// and backward kernels (private to them): per 128-row tile, NQ chunks of 8 columns
+// (NQ = columns / 8), each chunk's 128 rows contiguous at 16 bytes per row, so the 32
+// lanes of a warp (32 consecutive rows of the tile) write or read 512 contiguous bytes
+// per 16-byte access.  Element offset of chunk q of row r.
+template <int NQ>
+__device__ __forceinline__ int64_t chunk_off(int64_t r, int q) {
+    return (((r >> 7) * NQ + q) * 128 + (r & 127)) * 8;
+}
+__device__ __forceinline__ int64_t hg_off(int64_t r, int q) { return chunk_off<N_H / 8>(r, q); }
 
 struct FusedArgs {
     int B;                       // rows, a multiple of 128
@@ -451,9 +456,9 @@ struct FusedArgs {
     const bf16 *Wc[N_LAYERS];    // W_l [fan_out][fan_in], core layout, K = fan_in
     const bf16 *Wtc[N_LAYERS];   // W_l^T [fan_in][fan_out], core layout, K = fan_out (l >= 1)
     const float *theta;          // FP32 masters (biases)
-    bf16 *X;                     // [B][64]
+    bf16 *X;                     // B x 64 in the chunked layout of chunk_off
     bf16 *H[4], *G[4];           // B x 128 in the chunked layout of hg_off
-    bf16 *dY;                    // [B][16]
+    bf16 *dY;                    // B x 16 in the chunked layout of chunk_off
     float *loss, *grad;
     float gscale;
     int32_t *err;
@@ -612,8 +617,8 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
                 const uint4 wA = pack8(part + 8 * k), wB = pack8(part + 16 + 8 * k);
                 *reinterpret_cast<uint4 *>(act + cmo(row, cA + 8 * k, N_IN)) = wA;
                 *reinterpret_cast<uint4 *>(act + cmo(row, cB + 8 * k, N_IN)) = wB;
-                reinterpret_cast<uint4 *>(f.X + r * N_IN)[(cA >> 3) + k] = wA;
-                reinterpret_cast<uint4 *>(f.X + r * N_IN)[(cB >> 3) + k] = wB;
+                *reinterpret_cast<uint4 *>(f.X + chunk_off<N_IN / 8>(r, (cA >> 3) + k)) = wA;
+                *reinterpret_cast<uint4 *>(f.X + chunk_off<N_IN / 8>(r, (cB >> 3) + k)) = wB;
             }
         }
         float tg[N_OUT];
@@ -674,8 +679,8 @@ __global__ void __launch_bounds__(256 * NG, 1) k_mlp_fwd(FusedArgs f) {
                     }
                     dv[c] = __float2bfloat16(dy);
                 }
-                uint4 *dd = reinterpret_cast<uint4 *>(f.dY + r * N_OUT_PAD);
-                dd[0] = pack8(dv); dd[1] = pack8(dv + 8);
+                *reinterpret_cast<uint4 *>(f.dY + chunk_off<N_OUT_PAD / 8>(r, 0)) = pack8(dv);
+                *reinterpret_cast<uint4 *>(f.dY + chunk_off<N_OUT_PAD / 8>(r, 1)) = pack8(dv + 8);
             }
             tc::fence_before_sync();
         }
@@ -754,10 +759,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 hreg[k] = *reinterpret_cast<const uint4 *>(f.H[l - 1] + hg_off(rr, ((hw * half) >> 3) + k));
-        } else {  // X [B][64], row-major
-            const uint4 *hin = reinterpret_cast<const uint4 *>(f.X + rr * N_IN);
+        } else {  // X
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hreg[k] = hin[((hw * half) >> 3) + k];
+            for (int k = 0; k < 4; ++k)
+                hreg[k] = *reinterpret_cast<const uint4 *>(f.X + chunk_off<N_IN / 8>(rr, ((hw * half) >> 3) + k));
         }
     };
     auto store_h = [&](int l) {
@@ -773,9 +778,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     uint4 dyreg[2];  // the tile's output error row dY (half 0), fetched with the tile's H_4 rows
     auto load_dy = [&](int64_t rr) {
         if (half == 0) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(f.dY + rr * N_OUT_PAD);
-            dyreg[0] = src[0];
-            dyreg[1] = src[1];
+            dyreg[0] = *reinterpret_cast<const uint4 *>(f.dY + chunk_off<N_OUT_PAD / 8>(rr, 0));
+            dyreg[1] = *reinterpret_cast<const uint4 *>(f.dY + chunk_off<N_OUT_PAD / 8>(rr, 1));
         }
     };
     if (blockIdx.x < (f.B >> 7)) {
