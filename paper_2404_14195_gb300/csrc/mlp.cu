@@ -751,8 +751,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     };
     // Global rows are loaded into registers while the MMAs run: this half's columns of the
     // input of layer l (H_{l-1}, X for the first layer) for the next layer's staging, and of
-    // GELU'(Z_{l-1}) for this layer's epilogue.
-    uint4 hreg[8], greg[8];
+    // GELU'(Z_{l-2}) for the next layer's epilogue (gnext, moved into greg after this
+    // layer's epilogue), so each GELU' load has a layer's MMAs and epilogue to arrive.
+    uint4 hreg[8], greg[8], gnext[8];
     auto load_h = [&](int l, int64_t rr) {
         const int hw = fan_in(l) >> 1;
         if (l > 0) {
@@ -771,9 +772,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
         for (int k = 0; k < 8; ++k)
             if (k < (hw >> 3)) *reinterpret_cast<uint4 *>(Hs + cmo(row, hw * half + 8 * k, fi)) = hreg[k];
     };
-    auto load_g = [&](int l, int64_t rr) {
+    // GELU'(Z_{l-1}), read by the epilogue of layer l, into dst
+    auto load_g = [&](uint4 (&dst)[8], int l, int64_t rr) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) greg[k] = *reinterpret_cast<const uint4 *>(f.G[l - 1] + hg_off(rr, 8 * half + k));
+        for (int k = 0; k < 8; ++k) dst[k] = *reinterpret_cast<const uint4 *>(f.G[l - 1] + hg_off(rr, 8 * half + k));
     };
     uint4 dyreg[2];  // the tile's output error row dY (half 0), fetched with the tile's H_4 rows
     auto load_dy = [&](int64_t rr) {
@@ -785,6 +787,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     if (blockIdx.x < (f.B >> 7)) {
         load_h(N_LAYERS - 1, (int64_t)blockIdx.x * 128 + row);
         load_dy((int64_t)blockIdx.x * 128 + row);
+        load_g(greg, N_LAYERS - 1, (int64_t)blockIdx.x * 128 + row);
     }
     for (int tile = blockIdx.x; ok && tile < (f.B >> 7); tile += gridDim.x) {
         const int64_t r = (int64_t)tile * 128 + row;
@@ -809,11 +812,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             // the MMAs below no longer need the registers: fetch the next rows behind them
             auto prefetch = [&]() {
                 if (l > 0) {
-                    load_g(l, r);
+                    if (l >= 2) load_g(gnext, l - 1, r);
                     load_h(l - 1, r);
                 } else if (r_next >= 0) {
                     load_h(N_LAYERS - 1, r_next);
                     load_dy(r_next);
+                    load_g(gnext, N_LAYERS - 1, r_next);
                 }
             };
             if (l == N_LAYERS - 1) {
@@ -890,6 +894,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                 }
                 __syncthreads();
                 if (t < N_H) dbsum[(l - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
+            }
+            if (l >= 2 || (l == 0 && r_next >= 0)) {  // GELU' of the next epilogue
+#pragma unroll
+                for (int k = 0; k < 8; ++k) greg[k] = gnext[k];
             }
             tc::fence_before_sync();
         }
