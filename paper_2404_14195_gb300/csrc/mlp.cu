@@ -430,9 +430,10 @@ constexpr int TILE_BYTES = 2 * 128 * 128;
 constexpr int FW_NBIAS = 4 * 128 + N_OUT_PAD;
 // forward: weights, one activation tile per tile group (NG groups of 256 threads), biases
 constexpr size_t fw_smem(int ng) { return FW_WBYTES + ng * TILE_BYTES + 4 * FW_NBIAS + 64 + 1024; }
-// backward: W^T, the dZ and H tiles, column-sum scratch, per-CTA sums of db (5 x 128),
+// backward: W^T, the dZ and H tiles, per-CTA sums of db (5 layers x 4 row groups x 128),
 // dW_5^T (16 x 128) and dW_1 (64 x 128) in FP32
-constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * 128 * 4 + 4 * (5 * 128 + 16 * 128 + 64 * 128) + 64 + 1024;
+constexpr int FB_NSUM = 5 * 4 * 128 + 16 * 128 + 64 * 128;
+constexpr size_t FB_SMEM = FB_WBYTES + 2 * TILE_BYTES + 4 * FB_NSUM + 64 + 1024;
 
 // The features X, H_l, GELU'(Z_l) and the output error dY between the fused forward
 // and backward kernels (private to them): per 128-row tile, NQ chunks of 8 columns
@@ -707,14 +708,13 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     bf16 *An = reinterpret_cast<bf16 *>(p);                  // dZ_l [128 rows][fan_out], K = fan_out
     bf16 *Hs = reinterpret_cast<bf16 *>(p + TILE_BYTES);     // H_{l-1} [128 rows][fan_in]
     p += 2 * TILE_BYTES;
-    float *colsum = reinterpret_cast<float *>(p);             // [4 row groups][128 columns]
-    p += 4 * 128 * 4;
-    // this CTA's sums over its tiles, each entry owned by one thread: db_l [l][column]
-    // (thread = column), dW_5^T [out][in] and dW_1 [in][out] (thread = the TMEM lane's unit)
-    float *dbsum = reinterpret_cast<float *>(p);
-    float *dw5 = dbsum + 5 * 128;
+    // this CTA's sums over its tiles, each entry owned by one thread: db_l per warp row
+    // group [l][row group][column] (the lane that holds the column's warp sum), dW_5^T
+    // [out][in] and dW_1 [in][out] (thread = the TMEM lane's unit)
+    float *dbq = reinterpret_cast<float *>(p);
+    float *dw5 = dbq + 5 * 4 * 128;
     float *dw1 = dw5 + 16 * 128;
-    p += 4 * (5 * 128 + 16 * 128 + 64 * 128);
+    p += 4 * FB_NSUM;
     uint64_t *wbar = reinterpret_cast<uint64_t *>(p), *mbar = wbar + 1;
     uint32_t *slot = reinterpret_cast<uint32_t *>(wbar + 2);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     // TMEM columns: 0..127 dH_{l-1} of the current layer (also dW_5^T and dW_1 of the
     // current tile, read out at once); 128 l .. 128 l + 127 for l = 1, 2, 3: dW_{l+1}
     // summed over all of this CTA's tiles, added into the gradient once at the end
-    for (int e = threadIdx.x; e < 5 * 128 + 16 * 128 + 64 * 128; e += blockDim.x) dbsum[e] = 0.0f;
+    for (int e = threadIdx.x; e < FB_NSUM; e += blockDim.x) dbq[e] = 0.0f;
     if (warp == 0) {
         tc::tmem_alloc(slot, 512);
         tc::tmem_relinquish();
@@ -743,11 +743,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
     }
     bool ok = tc::mbar_wait(wbar, 0, WAIT_NS);
     uint32_t phase = 0;
-    // column sums of this thread's dz values over its warp's 32 rows, into colsum[wq][c0 ..]
-    auto colsum16 = [&](const float *dz, int c0) {
+    // column sums of this thread's dz values over its warp's 32 rows, added to db_l of the
+    // warp's row group (no barrier: each entry has one owner; the groups are summed at the end)
+    auto colsum16 = [&](const float *dz, int c0, int l) {
         int col;
         const float sv = warp_colsum16(dz, lane, col);
-        if ((lane & 1) == 0) colsum[wq * 128 + c0 + col] = sv;
+        if ((lane & 1) == 0) dbq[(l * 4 + wq) * 128 + c0 + col] += sv;
     };
     // Global rows are loaded into registers while the MMAs run: this half's columns of the
     // input of layer l (H_{l-1}, X for the first layer) for the next layer's staging, and of
@@ -801,10 +802,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
             float dz[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) dz[c] = __bfloat162float(dv[c]);
-            colsum16(dz, 0);
+            colsum16(dz, 0, N_LAYERS - 1);
         }
-        __syncthreads();
-        if (t < N_OUT_PAD) dbsum[(N_LAYERS - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
         for (int l = N_LAYERS - 1; l >= 0 && ok; --l) {
             const int fi = fan_in(l), fo = fan_out(l), hw = fi >> 1;
             store_h(l);  // the tile's rows of H_{l-1} (X for the first layer), this half's columns
@@ -890,10 +889,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     const bf16 *dv = reinterpret_cast<const bf16 *>(dv2);
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0, N_H)) = pack8(dv);
                     *reinterpret_cast<uint4 *>(An + cmo(row, c0 + 8, N_H)) = pack8(dv + 8);
-                    colsum16(dz, c0);
+                    colsum16(dz, c0, l - 1);
                 }
-                __syncthreads();
-                if (t < N_H) dbsum[(l - 1) * 128 + t] += colsum[t] + colsum[128 + t] + colsum[256 + t] + colsum[384 + t];
             }
             if (l >= 2 || (l == 0 && r_next >= 0)) {  // GELU' of the next epilogue
 #pragma unroll
@@ -916,8 +913,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bwd(FusedArgs f) {
                     if (v != 0.0f) atomicAdd(f.grad + w_off_c(N_LAYERS - 1) + o * N_H + row, v);
                 }
             if (t < N_H)
-                for (int l = 0; l < N_LAYERS; ++l) {
-                    const float v = dbsum[l * 128 + t];
+                for (int l = 0; l < N_LAYERS; ++l) {  // (written before the last layer's barrier)
+                    const float *q = dbq + l * 4 * 128 + t;
+                    const float v = q[0] + q[128] + q[256] + q[384];
                     if (v != 0.0f && (l < N_LAYERS - 1 || t < N_OUT_PAD)) atomicAdd(f.grad + b_off_c(l) + t, v);
                 }
         }
