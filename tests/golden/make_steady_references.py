@@ -10,7 +10,7 @@ one window, and records k, K, the steps taken and the last window's change.
   python tests/golden/make_steady_references.py [name ...]   (default: all)
 
 The config-2 MLBM entry takes about an hour on 8 cores, each held-out entry of
-the warm-start experiment a few minutes.
+the warm-start experiment and the config-4-family entry a few minutes.
 """
 from __future__ import annotations
 
